@@ -1,0 +1,199 @@
+"""Physics pins of the FP64 oracle (no GPU).
+
+P5 conservation in a periodic box (Eq. 2.3, s^(0) = 0 of Eq. 3.2):
+   with H_i on and no force, mass, momentum and energy stay constant to
+   round-off; with F^SC + P_i, mass and momentum do; a uniform acceleration
+   raises the momentum by exactly g * mass per step.
+P6 shear wave: decay rate nu k^2 with nu = c0^2 (tau^ - 1/2) (Sec. 5.1).
+P7 Prandtl number: the entropy mode decays at (nu / Pr) k^2 with H_i
+   (Eqs. 3.4-3.7) and at nu k^2 with BGK alone (Pr = 1, Sec. 1).
+P8 Kolmogorov flow start-up against its closed form.
+P9 equations of state: critical temperatures (Sec. 5.4: T_c ~ 0.023 for
+   Carnahan-Starling), the equal-area rule against the closed-form chemical
+   potentials, and the flat interface: without P_i (k = 0) the gas density is
+   underestimated (Sec. 3.3), with the tuned k both densities are within 2%
+   of Maxwell's and the bulk pressures of the two phases agree.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import analytic, eos, lattice
+from oracle.solver import Oracle
+import workloads as W
+
+
+def _smooth_fields(nx, ny, amp=0.02):
+    x = 2 * np.pi * np.arange(nx)[None, :] / nx
+    y = 2 * np.pi * np.arange(ny)[:, None] / ny
+    rho = 1.0 + amp * np.sin(x) * np.cos(2 * y)
+    u = np.stack([amp * np.cos(y + x), np.broadcast_to(amp * np.sin(2 * x), (ny, nx))])
+    theta = 1.0 + amp * np.cos(x - y)
+    return rho, u, theta
+
+
+def test_conservation_thermal_source():
+    rho, u, th = _smooth_fields(16, 16)
+    o = Oracle("D2Q37", 16, 16, 1, 0.7, W.source_params(H=True, Pr=0.71))
+    o.init(rho, u, th)
+    d0 = o.diag()
+    o.run(1000)
+    d1 = o.diag()
+    assert abs(d1[0] - d0[0]) <= 1e-12 * d0[0]
+    assert np.all(np.abs(d1[1:3] - d0[1:3]) <= 1e-12 * d0[0])
+    assert abs(d1[3] - d0[3]) <= 1e-12 * d0[3]
+
+
+def test_conservation_pseudopotential():
+    c = W.droplet(n=32, r0=8.0, tau_hat=0.8, k=1.0)
+    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    d0 = o.diag()
+    o.run(300)
+    d1 = o.diag()
+    assert np.isfinite(d1).all()
+    assert abs(d1[0] - d0[0]) <= 1e-12 * d0[0]
+    assert np.all(np.abs(d1[1:3] - d0[1:3]) <= 1e-12 * d0[0])
+
+
+def test_uniform_force_momentum_budget():
+    rho, u, th = _smooth_fields(12, 10)
+    g = (2e-5, -1e-5, 0.0)
+    o = Oracle("D2Q37", 12, 10, 1, 0.9, W.source_params(force=True, g=g))
+    o.init(rho, u, th)
+    d0 = o.diag()
+    o.run(50)
+    d1 = o.diag()
+    M = d0[0]
+    assert np.allclose(d1[1:3] - d0[1:3], 50 * M * np.array(g[:2]), rtol=1e-10, atol=1e-14)
+
+
+def test_shear_wave_viscosity():
+    c = W.shear_wave(nx=8, ny=128, tau_hat=0.8, u0=1e-3)
+    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    s = np.sin(2 * np.pi * np.arange(128) / 128)
+
+    def amp():
+        _, u, _ = o.moments()
+        return (u[0].mean(axis=1) * s).sum() / (s * s).sum()
+
+    o.run(100)
+    a1 = amp()
+    o.run(1000)
+    a2 = amp()
+    nu = analytic.viscosity(o.L.cs2, 0.8)
+    rate = np.log(a1 / a2) / 1000
+    assert abs(rate / analytic.shear_wave_rate(nu, 128) - 1) < 5e-3
+
+
+def _entropy_rate(Pr, H, nx=128, tau_hat=0.7):
+    c = W.thermal_decay(nx=nx, ny=8, tau_hat=tau_hat, Pr=Pr, noise=0, u0=0.0, eps_T=1e-4, H=H)
+    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    s = np.sin(2 * np.pi * np.arange(nx) / nx)
+    nu = analytic.viscosity(o.L.cs2, tau_hat)
+    k2 = analytic.entropy_mode_rate(nu, Pr, nx)
+    o.run(int(0.2 / k2))
+    ts, am = [], []
+    T1 = int(1.0 / k2)
+    stride = max(1, T1 // 200)
+    for t in range(0, T1, stride):
+        _, _, th = o.moments()
+        ts.append(t)
+        am.append(((th.mean(axis=0) - 1.0) * s).sum() / (s * s).sum())
+        o.run(stride)
+    # least squares over many acoustic periods (sound waves ride on the decay)
+    slope = np.polyfit(ts, np.log(am), 1)[0]
+    return -slope, k2
+
+
+@pytest.mark.parametrize("Pr,H", [(0.71, True), (1.41, True), (1.0, False)])
+def test_prandtl_number(Pr, H):
+    rate, expect = _entropy_rate(Pr, H)
+    assert abs(rate / expect - 1) < 1e-2, (rate, expect)
+
+
+def test_prandtl_literal_table2_factor_is_rejected():
+    """Table 2 prints (1 - 1/(c0^2 Pr)); it would give an effective Pr of c0^2 Pr,
+    a decay rate 1/c0^2 = 1.43 times the one measured above."""
+    rate, expect = _entropy_rate(0.71, True)
+    L = lattice.d2q37()
+    nu = analytic.viscosity(L.cs2, 0.7)
+    literal = analytic.entropy_mode_rate(nu, L.cs2 * 0.71, 128)
+    assert abs(rate / literal - 1) > 0.2
+
+
+def test_kolmogorov_start_up():
+    c = W.kolmogorov(64)
+    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.set_force_field(c.gfield)
+    o.init(c.rho, c.u, c.theta)
+    o.run(2000)
+    _, u, _ = o.moments()
+    nu = analytic.viscosity(o.L.cs2, c.tau_hat)
+    ua = analytic.kolmogorov_ux(np.arange(64), 2000, c.meta["g0"], nu, 64)
+    err = np.abs(u[0] - ua[:, None]).max() / np.abs(ua).max()
+    assert err < 1e-2, err
+    assert np.abs(u[1]).max() < 1e-3 * np.abs(ua).max()
+
+
+def test_critical_temperatures():
+    assert abs(eos.critical_temperature("vdw", W.VDW_A, W.VDW_B) - 4.0 / 7.0) < 1e-7
+    tc = eos.critical_temperature("cs", 0.25, 4.0)
+    assert 0.023 <= tc < 0.024          # "T_c ~ 0.023" (Sec. 5.4)
+
+
+def _mu_vdw(rho, a, b, T):
+    # chemical potential of the van der Waals fluid (closed form of d f / d rho)
+    return T * np.log(rho / (1.0 - b * rho)) + T * b * rho / (1.0 - b * rho) - 2.0 * a * rho
+
+
+def _mu_cs(rho, a, b, T):
+    e = b * rho / 4.0
+    return T * np.log(rho) + T * (8 * e - 9 * e * e + 3 * e ** 3) / (1.0 - e) ** 3 - 2.0 * a * rho
+
+
+@pytest.mark.parametrize("kind,Tr", [("vdw", 0.7), ("vdw", 0.85), ("vdw", 0.95), ("cs", 0.7), ("cs", 0.9)])
+def test_maxwell_equal_chemical_potential(kind, Tr):
+    a, b = (W.VDW_A, W.VDW_B) if kind == "vdw" else (0.25, 4.0)
+    T = Tr * eos.critical_temperature(kind, a, b)
+    rg, rl, ps = eos.maxwell(kind, a, b, T)
+    mu = _mu_vdw if kind == "vdw" else _mu_cs
+    assert rg < rl
+    assert abs(mu(rg, a, b, T) - mu(rl, a, b, T)) < 1e-9 * max(1.0, abs(mu(rg, a, b, T)))
+    assert abs(eos.pressure(kind, rg, a, b, T) - ps) < 1e-12
+    assert abs(eos.pressure(kind, rl, a, b, T) - ps) < 1e-12
+
+
+def test_tabulated_coexistence_densities():
+    for Tr, (rg, rl) in W.VDW_COEXIST.items():
+        g, l, _ = eos.maxwell("vdw", W.VDW_A, W.VDW_B, Tr * W.VDW_TC)
+        assert abs(g - rg) < 1e-9 and abs(l - rl) < 1e-9
+
+
+def _flat_interface(k, steps=10000):
+    c = W.flat_interface(nx=8, ny=200, tau_hat=0.8, Tr=0.85, k=k)
+    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    o.run(steps)
+    rho, _, _ = o.moments()
+    return rho[0, 0], rho[100, 0], c
+
+
+def test_flat_interface_without_pressure_source_underestimates_gas():
+    rg, rl, c = _flat_interface(0.0, 5000)
+    assert rg < 0.95 * c.meta["rho_g"]
+
+
+def test_flat_interface_tuned_k_matches_maxwell():
+    path = os.path.join(os.path.dirname(__file__), "golden", "vdw_flat_interface_k.txt")
+    k = float([ln for ln in open(path) if not ln.startswith("#")][0])
+    rg, rl, c = _flat_interface(k)
+    assert abs(rg / c.meta["rho_g"] - 1) < 2e-2
+    assert abs(rl / c.meta["rho_l"] - 1) < 2e-2
+    p = c.params
+    pg = eos.pressure("vdw", rg, p["eos_a"], p["eos_b"], p["eos_T"])
+    pl = eos.pressure("vdw", rl, p["eos_a"], p["eos_b"], p["eos_T"])
+    assert abs(pg - pl) < 2e-2 * pl
