@@ -1,0 +1,362 @@
+"""Throughput of the fused high-order lattice Boltzmann step on GB300.
+
+Workload: D2Q37 thermal decay with the Prandtl-number source H_i, 1024 x 1024
+periodic, tau^ = 0.7, Pr = 0.71 (theta = 1 + 0.01 sin(2 pi x/1024),
+rho = 1/theta + 1e-6 seeded noise, u_x = 0.01 sin(2 pi y/1024)); one step =
+one launch of the fused pull-collide-source kernel over all 1,048,576 nodes.
+
+Metric: MLUPS (million lattice-node updates per second), whole job over all
+ranks.  The population buffers (2 x 155 MB in FP32) are larger than the
+129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|f16|bf16]
+                  [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on the host cores over a 256 x 256 sample of the same workload.
+Multi-GPU (torchrun): every rank advances its own independent replica of the
+domain (no data-path collective; "replicas only"), timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "D2Q37 thermal decay + H_i (Pr=0.71), 1024x1024 periodic, tau=0.7"
+METRIC = "MLUPS"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2411_10751_gb300" / "csrc").glob("*")):
+        if f.suffix in (".cu", ".cuh", ".h", ".cpp"):
+            h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_hash: str, storage: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was captured from the current kernel sources; else None."""
+    p = ROOT / "profiles" / "fused_step_thermal1024_dram.json"
+    if not p.exists():
+        return None
+    try:
+        d = json.loads(p.read_text())
+    except ValueError:
+        return None
+    e = d.get(storage)
+    if not e or d.get("kernel_source_sha") != kernel_hash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_device(case, storage, steps, warmup, ws, lrank):
+    """Device-resident run: K steps timed with CUDA events on the context's stream."""
+    import torch
+    from paper_2411_10751_gb300.solver import HLBM
+    g = HLBM(case.lattice, case.nx, case.ny, 1, case.tau_hat, case.params, storage=storage, device=lrank)
+    g.init(case.rho, case.u, case.theta)
+    g.step(warmup)
+    g.synchronize()
+    s = g.cuda_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(lrank) as clk:
+        e0.record(s)
+        g.step(steps)
+        e1.record(s)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    ms = e0.elapsed_time(e1)
+    d = g.diag()
+    g.close()
+    return ms, clk.summary(), d
+
+
+def time_e2e(case, storage, steps, ws, lrank):
+    """Through the public API with host buffers: pinned host fields -> hlbm_init
+    (H2D), K steps, hlbm_moments to pinned host buffers (D2H); wall time."""
+    import torch
+    from paper_2411_10751_gb300.solver import HLBM
+    g = HLBM(case.lattice, case.nx, case.ny, 1, case.tau_hat, case.params, storage=storage, device=lrank)
+    pin = {k: torch.from_numpy(np.asarray(getattr(case, k), np.float32)).pin_memory() for k in ("rho", "u", "theta")}
+    out = {k: torch.empty_like(pin[k]).pin_memory() for k in pin}
+    g.init(pin["rho"].numpy(), pin["u"].numpy(), pin["theta"].numpy())   # warm-up of the path
+    g.synchronize()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    from paper_2411_10751_gb300 import abi
+    abi.check(abi.hlbm_init(g.ctx, pin["rho"].data_ptr(), pin["u"].data_ptr(), pin["theta"].data_ptr(), 0), g.ctx)
+    abi.check(abi.hlbm_step(g.ctx, steps), g.ctx)
+    abi.check(abi.hlbm_moments(g.ctx, out["rho"].data_ptr(), out["u"].data_ptr(), out["theta"].data_ptr(), 0), g.ctx)
+    t1 = time.perf_counter()
+    _barrier(ws)
+    h2d = sum(t.numel() * 4 for t in pin.values())
+    d2h = sum(t.numel() * 4 for t in out.values())
+    assert np.isfinite(out["u"].numpy()).all()
+    g.close()
+    return (t1 - t0) * 1e3, h2d, d2h
+
+
+def storage_errors(n=256, steps=100):
+    """Per-field error of each storage against the FP64 oracle on an n^2 copy of the workload."""
+    from oracle.solver import Oracle
+    from paper_2411_10751_gb300.solver import HLBM
+    c = W.thermal_decay(n=n)
+    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    o.run(steps)
+    r0, u0, t0 = o.moments()
+    res = {}
+    for st in ("f32", "f16", "bf16"):
+        g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params, storage=st)
+        g.init(c.rho, c.u, c.theta)
+        g.step(steps)
+        r, u, t = g.moments_host()
+        g.close()
+        res[st] = {"rho": float(np.abs(r - r0).max() / np.abs(r0).max()),
+                   "u": float(np.sqrt(((u - u0) ** 2).sum(0)).max() / np.sqrt((u0 ** 2).sum(0)).max()),
+                   "theta": float(np.abs(t - t0).max() / np.abs(t0).max())}
+    return {"case": f"{n}x{n} copy of the workload, {steps} steps, max|q-q_oracle|/max|q_oracle|", **res}
+
+
+def cpu_baseline(budget_s=12.0, n=1024):
+    """FP64 oracle on the host cores over the full 1024^2 workload, as many
+    whole steps as fit in about budget_s seconds (at least 2)."""
+    from oracle import solver as osol
+    c = W.thermal_decay(n=n)
+    o = osol.Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    o.run(1)
+    t0 = time.perf_counter()
+    k = 0
+    while k < 2 or time.perf_counter() - t0 < budget_s:
+        o.run(1)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": c.nodes * k / dt / 1e6, "unit": METRIC, "cores": osol.get_threads(), "kind": "oracle",
+            "sample": f"{k} FP64 oracle steps of the full {n}x{n} workload ({dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from oracle import solver as osol
+    osol.build()
+    n = 256
+    c = W.thermal_decay(n=n)
+    o = osol.Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    o.init(c.rho, c.u, c.theta)
+    o.run(args.warmup)
+    t0 = time.perf_counter()
+    o.run(args.steps)
+    dt = time.perf_counter() - t0
+    v = c.nodes * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}x{n} of the workload"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": osol.get_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle steps on a {n}x{n} sample of the workload"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, lrank = _dist()
+
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl")
+    import paper_2411_10751_gb300 as pkg
+    if rank == 0 or ws == 1:
+        pkg.build()
+    _barrier(ws)
+    pkg.load()
+
+    case = W.thermal_decay(n=1024)
+    ms, clocks, diag = time_device(case, args.storage, args.steps, args.warmup, ws, lrank)
+    ms = _max_over_ranks(ws, ms)
+    nodes = case.nodes
+    value = nodes * args.steps * ws / (ms * 1e-3) / 1e6
+    elem = 4 if args.storage == "f32" else 2
+    bytes_per_node = 2 * 37 * elem
+    launch_s = ms * 1e-3 / args.steps
+    achieved = bytes_per_node * nodes / launch_s / 1e9
+    peak, peak_kind = _peaks()
+    khash = _kernel_source_hash()
+
+    e2e_ms, h2d, d2h = time_e2e(case, args.storage, args.steps, ws, lrank)
+    e2e_ms = _max_over_ranks(ws, e2e_ms)
+
+    variants = None
+    errors = None
+    cpu = None
+    if rank == 0:
+        if not args.no_variants:
+            variants = {}
+            for st in ("f32", "f16", "bf16"):
+                if st == args.storage:
+                    continue
+                k = min(args.steps, 4000)
+                vms, _, _ = time_device(case, st, k, args.warmup, 1, lrank)
+                e = 4 if st == "f32" else 2
+                variants[st] = {"MLUPS": nodes * k / (vms * 1e-3) / 1e6,
+                                "achieved_GBs": 2 * 37 * e * nodes / (vms * 1e-3 / k) / 1e9,
+                                "frac_of_" + peak_kind: 2 * 37 * e * nodes / (vms * 1e-3 / k) / 1e9 / peak}
+            errors = storage_errors()
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes_per_gpu": nodes, "storage": args.storage,
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (2 x %d MB population buffers), no flush" %
+                             (37 * elem * nodes // 2 ** 20)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": _ncu_traffic(khash, args.storage),
+                         "algorithmic_bytes_per_node": bytes_per_node, "kernel": "step2d_kernel (KIND_THERMAL)"},
+            "e2e": {"value": nodes * args.steps * ws / (e2e_ms * 1e-3) / 1e6, "unit": METRIC,
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "path": "hlbm_init(host) + hlbm_step(K) + hlbm_moments(host), pinned host buffers"},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "storage_variants": variants,
+            "storage_error_vs_oracle": errors,
+            "final_diag": [float(x) for x in diag],
+            "kernel_source_sha": khash,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * hlbm: one fused time step of the high-order (multi-speed) BGK lattice
+ * Boltzmann method with Hermite-polynomial body sources, after
+ * S. Li et al., "Constructing the body source for high-order lattice
+ * Boltzmann method", on one NVIDIA GB300 (sm_103a).
+ *
+ * The step (Eq. 4.4 with the shift of Eq. 4.3) on D2Q37 (Sec. 4.1, Table 1)
+ * or D3Q39 is
+ *     f^_i(x + c_i, t + 1) = f^_i - (f^_i - f^eq_i) / tau^ + (1 - 1 / (2 tau^)) S_i
+ * with the 4th-order Hermite equilibrium (Eq. 2.2, 3rd order on D3Q39), the
+ * moments of Eq. 4.5 (half-source shift), and S_i = F_i + H_i + P_i:
+ *   F_i  body force (Eqs. 3.1-3.3), force density F = rho g + F^SC
+ *   H_i  thermal diffusion source setting the Prandtl number (Eqs. 3.4-3.7),
+ *        grad theta by second-order central differences
+ *   F^SC pseudopotential force (Eq. 3.8) over the lattice's reach-3 stencil
+ *   P_i  pressure-tensor source (Eqs. 3.10-3.12)
+ * All sources at time t use fields of time t at every node (no time lag).
+ * Domains are periodic in every direction.
+ *
+ * Conventions
+ *   Units: lattice units (dx = dt = 1), integer velocities c_i, lattice
+ *     temperature c0^2 theta; tau_hat is the shifted relaxation time tau^,
+ *     so the kinematic viscosity is c0^2 theta (tau_hat - 1/2).
+ *   Field layout (row-major, x fastest): scalar fields [nz][ny][nx];
+ *     vector fields [D][nz][ny][nx] (nz = 1 in 2D).
+ *   Memory: "on_device" = 1 means the pointer is CUDA device memory, 0 means
+ *     host memory (the call then copies and synchronises its stream).
+ *     Input pointers are borrowed for the duration of the call only.
+ *   Streams: every call is ordered on the context's stream
+ *     (hlbm_set_stream); calls that return host data synchronise it.
+ *   Errors: every call returns an hlbm_status; hlbm_last_error gives the
+ *     message.  After a CUDA error or a detected divergence the context is
+ *     in an error state and further calls return HLBM_ESTATE until it is
+ *     destroyed or reloaded with hlbm_load.
+ *   Threading: a context must not be used from two threads at once.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { HLBM_D2Q37 = 0, HLBM_D3Q39 = 1 } hlbm_lattice;
+
+/* Storage of the populations.  The stored quantity is always the
+ * Hermite-normalised deviation g_i = (f^_i - w_i rho0) / w_i; arithmetic is
+ * FP32 in every case. */
+typedef enum { HLBM_F32 = 0, HLBM_F16 = 1, HLBM_BF16 = 2 } hlbm_storage;
+
+typedef enum {
+  HLBM_OK = 0,
+  HLBM_EINVAL = 1,       /* invalid argument */
+  HLBM_ENOMEM = 2,       /* allocation failed or bound memory too small */
+  HLBM_ECUDA = 3,        /* a CUDA call failed */
+  HLBM_EDIVERGED = 4,    /* non-finite or non-positive density found */
+  HLBM_ETIMEOUT = 5,     /* a bounded device wait expired */
+  HLBM_ESTATE = 6,       /* context is in an error state */
+  HLBM_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} hlbm_status;
+
+/* source flags */
+#define HLBM_SRC_FORCE 1u      /* body force F_i (Eq. 3.3), F = rho g */
+#define HLBM_SRC_H 2u          /* thermal diffusion source H_i (Eq. 3.7) */
+#define HLBM_SRC_SC 4u         /* pseudopotential force F^SC (Eq. 3.8) */
+#define HLBM_SRC_P 8u          /* pressure-tensor source P_i (Eq. 3.12), needs SC */
+#define HLBM_ISOTHERMAL 16u    /* theta == 1 in f^eq and F_i (Sec. 5.4); required by SC */
+
+typedef struct {
+  uint32_t flags;     /* HLBM_SRC_* | HLBM_ISOTHERMAL */
+  double force[3];    /* uniform acceleration g when no force field is set */
+  double Pr;          /* Prandtl number for H_i (Sec. 3.2), > 0 */
+  int eos;            /* 0: van der Waals p = rho T/(1 - b rho) - a rho^2;
+                         1: Carnahan-Starling (Eq. 5.9), R = 1 */
+  double eos_a, eos_b, eos_T;  /* EOS parameters a, b and temperature T */
+  double k;           /* free parameter k of Eq. 3.12 */
+  double rho0;        /* reference density of the stored deviations, > 0 */
+  int storage;        /* hlbm_storage */
+} hlbm_source_params;
+
+typedef struct hlbm_ctx hlbm_ctx;
+
+/* Bytes of device memory a context needs (two population buffers, the force
+ * field when HLBM_SRC_FORCE is set, diagnostics scratch).  0 on bad input. */
+size_t hlbm_workspace_bytes(int lattice, int nx, int ny, int nz, const hlbm_source_params* p);
+
+/* Creates a context.  nx, ny (and nz for D3Q39) >= 7 so that the reach-3
+ * velocities do not alias on the periodic grid; nz must be 1 for D2Q37;
+ * nx*ny*nz < 2^31; tau_hat > 1/2.  HLBM_SRC_SC requires HLBM_ISOTHERMAL,
+ * HLBM_SRC_H forbids it.  No device memory is allocated until the first call
+ * that needs it (or hlbm_bind_memory). */
+hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat,
+                        const hlbm_source_params* params, hlbm_ctx** out);
+
+/* Uses caller-owned device memory of at least hlbm_workspace_bytes() bytes,
+ * 256-byte aligned, instead of allocating.  The caller keeps it alive until
+ * hlbm_destroy.  Must precede hlbm_init. */
+hlbm_status hlbm_bind_memory(hlbm_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Orders all work of the context on this cudaStream_t (0: a private stream
+ * that synchronises with the legacy default stream). */
+hlbm_status hlbm_set_stream(hlbm_ctx* ctx, void* cuda_stream);
+
+/* The cudaStream_t the context orders its work on (its private stream is
+ * created here if none was set); NULL on error.  Lets callers time or
+ * order their own work against the context's. */
+void* hlbm_get_stream(hlbm_ctx* ctx);
+
+/* Initial state f^_i = f^eq_i(rho, u, theta) with no non-equilibrium part.
+ * rho, theta: [nz][ny][nx]; u: [D][nz][ny][nx]; FP32. Resets the step count. */
+hlbm_status hlbm_init(hlbm_ctx* ctx, const float* rho, const float* u, const float* theta,
+                      int on_device);
+
+/* Body-force acceleration field (F = rho g).  kind 0: none (the uniform
+ * params->force is used); kind 1: full field [D][nz][ny][nx]; kind 2: a
+ * profile along y, [D][ny] (the same at every x and z).  The data are copied. */
+hlbm_status hlbm_set_force_field(hlbm_ctx* ctx, const float* g, int kind, int on_device);
+
+/* Advances n >= 0 time steps, asynchronously on the context's stream. */
+hlbm_status hlbm_step(hlbm_ctx* ctx, int n);
+
+/* rho, u, theta at the current time (Eq. 4.5, theta from the moments even in
+ * isothermal mode).  Any output pointer may be NULL. */
+hlbm_status hlbm_moments(hlbm_ctx* ctx, float* rho, float* u, float* theta, int on_device);
+
+/* FP64 sums over the domain: out[0] mass sum rho, out[1..D] momentum
+ * sum rho u, out[D+1] energy sum rho (|u|^2 + D c0^2 theta) / 2 (Eq. 2.3
+ * invariants).  Synchronises.  Returns HLBM_EDIVERGED (and enters the error
+ * state) if any node has a non-finite moment or rho <= 0. */
+hlbm_status hlbm_diag(hlbm_ctx* ctx, double* out);
+
+/* Checkpoint: size in bytes, then a copy of the populations and step count
+ * into / out of host memory.  save/load synchronise; load clears the error
+ * state.  A run of a + b steps equals a steps, save, load, b steps, bit for bit. */
+size_t hlbm_state_bytes(const hlbm_ctx* ctx);
+hlbm_status hlbm_save(hlbm_ctx* ctx, void* host_buf, size_t bytes);
+hlbm_status hlbm_load(hlbm_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Steps taken since hlbm_init / hlbm_load. */
+long long hlbm_step_count(const hlbm_ctx* ctx);
+
+/* Tile rows per CTA of the fused step (2D: 4, 8 or 16; 0 = default).  Used by
+ * the autotuner; results do not depend on it. */
+hlbm_status hlbm_set_tile(hlbm_ctx* ctx, int rows);
+
+/* Waits for all work on the context's stream. */
+hlbm_status hlbm_synchronize(hlbm_ctx* ctx);
+
+/* Message of the last failing call on this context (never NULL). */
+const char* hlbm_last_error(const hlbm_ctx* ctx);
+
+hlbm_status hlbm_destroy(hlbm_ctx* ctx);
+
+/* Quadrature of a lattice as compiled into the library: c[Q*3] (int),
+ * w[Q], *cs2 = c0^2, returns Q (0 on bad lattice).  Any pointer may be NULL. */
+int hlbm_lattice_info(int lattice, int* c, double* w, double* cs2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HLBM_H */

@@ -1,0 +1,537 @@
+// Host implementation of the hlbm C ABI (include/hlbm.h): validation,
+// device memory (own allocation or a caller-bound arena), stream ordering,
+// CUDA-graph replay of the step loop, diagnostics and checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "hlbm.h"
+#include "internal.h"
+#include "lattice.cuh"
+
+using namespace hlbm;
+
+struct hlbm_ctx {
+  int lattice = 0, D = 2, Q = 37;
+  int nx = 0, ny = 0, nz = 1;
+  long long N = 0;
+  double tau_hat = 1.0;
+  hlbm_source_params p{};
+  int kind = KIND_LOCAL;
+  int storage = ST_F32;
+  size_t elem = 4;
+  int rows = 8;
+
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own_arena = false;
+  void* pop[2] = {nullptr, nullptr};
+  float* gfield = nullptr;
+  double* partials = nullptr;
+  double* red = nullptr;
+  int cur = 0;
+  bool initialised = false;
+
+  int force_mode = FORCE_NONE;
+  long long steps = 0;
+
+  bool failed = false;
+  std::string msg;
+
+  // graphs replaying kGraphSteps steps from buffer parity 0 / 1
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+static const int kGraphSteps = 32;  // even: a replay returns to the same buffer parity
+
+namespace {
+
+struct Layout {
+  size_t pop_bytes, off_pop1, off_g, off_part, off_red, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) {
+  Layout L{};
+  const long long N = (long long)nx * ny * nz;
+  const int Q = lattice == 0 ? 37 : 39, D = lattice == 0 ? 2 : 3;
+  const size_t elem = (p->storage == HLBM_F32) ? 4 : 2;
+  L.pop_bytes = align256((size_t)Q * (size_t)N * elem);
+  L.off_pop1 = L.pop_bytes;
+  L.off_g = L.off_pop1 + L.pop_bytes;
+  const size_t gbytes = (p->flags & HLBM_SRC_FORCE) ? align256((size_t)D * (size_t)N * 4) : 0;
+  L.off_part = L.off_g + gbytes;
+  L.off_red = L.off_part + align256((size_t)moment_blocks(lattice, nx, ny, nz) * 8 * sizeof(double));
+  L.total = L.off_red + 256;
+  return L;
+}
+
+hlbm_status fail(hlbm_ctx* c, hlbm_status st, const std::string& m, bool sticky = false) {
+  if (c) {
+    c->msg = m;
+    if (sticky) c->failed = true;
+  }
+  return st;
+}
+
+hlbm_status cuda_fail(hlbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, HLBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e), true);
+}
+
+#define HLBM_CUDA(c, call, where)                 \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+bool finite(double v) { return std::isfinite(v); }
+
+hlbm_status validate(int lattice, int nx, int ny, int nz, double tau_hat, const hlbm_source_params* p,
+                     std::string& why) {
+  if (!p) { why = "params is NULL"; return HLBM_EINVAL; }
+  if (lattice != HLBM_D2Q37 && lattice != HLBM_D3Q39) { why = "unknown lattice"; return HLBM_EINVAL; }
+  if (nx < 7 || ny < 7) { why = "nx and ny must be >= 7 (reach-3 velocities)"; return HLBM_EINVAL; }
+  if (lattice == HLBM_D2Q37 && nz != 1) { why = "nz must be 1 on D2Q37"; return HLBM_EINVAL; }
+  if (lattice == HLBM_D3Q39 && nz < 7) { why = "nz must be >= 7 on D3Q39"; return HLBM_EINVAL; }
+  if ((long long)nx * ny * nz >= (1LL << 31)) { why = "nx*ny*nz must be < 2^31"; return HLBM_EINVAL; }
+  if (!finite(tau_hat) || !(tau_hat > 0.5)) { why = "tau_hat must be finite and > 1/2"; return HLBM_EINVAL; }
+  if (p->storage < HLBM_F32 || p->storage > HLBM_BF16) { why = "unknown storage"; return HLBM_EINVAL; }
+  if (!finite(p->rho0) || !(p->rho0 > 0)) { why = "rho0 must be finite and > 0"; return HLBM_EINVAL; }
+  const uint32_t known = HLBM_SRC_FORCE | HLBM_SRC_H | HLBM_SRC_SC | HLBM_SRC_P | HLBM_ISOTHERMAL;
+  if (p->flags & ~known) { why = "unknown flag bits"; return HLBM_EINVAL; }
+  for (int d = 0; d < 3; ++d)
+    if (!finite(p->force[d])) { why = "force must be finite"; return HLBM_EINVAL; }
+  if ((p->flags & HLBM_SRC_H) && (!finite(p->Pr) || !(p->Pr > 0))) { why = "Pr must be > 0"; return HLBM_EINVAL; }
+  if ((p->flags & HLBM_SRC_H) && (p->flags & HLBM_ISOTHERMAL)) {
+    why = "the thermal diffusion source needs the thermal mode"; return HLBM_EINVAL;
+  }
+  if ((p->flags & HLBM_SRC_SC) && !(p->flags & HLBM_ISOTHERMAL)) {
+    why = "the pseudopotential force needs the isothermal mode (theta == 1)"; return HLBM_EINVAL;
+  }
+  if ((p->flags & HLBM_SRC_P) && !(p->flags & HLBM_SRC_SC)) {
+    why = "the pressure-tensor source needs the pseudopotential force"; return HLBM_EINVAL;
+  }
+  if (p->flags & HLBM_SRC_SC) {
+    if (p->eos != 0 && p->eos != 1) { why = "eos must be 0 (vdW) or 1 (C-S)"; return HLBM_EINVAL; }
+    if (!finite(p->eos_a) || !finite(p->eos_b) || !finite(p->eos_T) || !finite(p->k) || !(p->eos_b > 0) ||
+        !(p->eos_T > 0)) {
+      why = "EOS parameters must be finite with b, T > 0"; return HLBM_EINVAL;
+    }
+  }
+  if (lattice == HLBM_D3Q39 && (p->flags & (HLBM_SRC_H | HLBM_SRC_SC))) {
+    why = "D3Q39 supports the body-force source only"; return HLBM_EUNSUPPORTED;
+  }
+  return HLBM_OK;
+}
+
+hlbm_status ensure_memory(hlbm_ctx* c) {
+  if (c->arena) return HLBM_OK;
+  const char* inj = std::getenv("HLBM_FAULT_ALLOC");
+  if (inj && inj[0] == '1') return fail(c, HLBM_ENOMEM, "device allocation failed (injected by HLBM_FAULT_ALLOC)");
+  const Layout L = layout(c->lattice, c->nx, c->ny, c->nz, &c->p);
+  void* m = nullptr;
+  cudaError_t e = cudaMalloc(&m, L.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HLBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->arena = static_cast<char*>(m);
+  c->arena_bytes = L.total;
+  c->own_arena = true;
+  return HLBM_OK;
+}
+
+void carve(hlbm_ctx* c) {
+  const Layout L = layout(c->lattice, c->nx, c->ny, c->nz, &c->p);
+  c->pop[0] = c->arena;
+  c->pop[1] = c->arena + L.off_pop1;
+  c->gfield = (c->p.flags & HLBM_SRC_FORCE) ? reinterpret_cast<float*>(c->arena + L.off_g) : nullptr;
+  c->partials = reinterpret_cast<double*>(c->arena + L.off_part);
+  c->red = reinterpret_cast<double*>(c->arena + L.off_red);
+}
+
+hlbm_status ensure_stream(hlbm_ctx* c) {
+  if (c->stream) return HLBM_OK;
+  HLBM_CUDA(c, cudaStreamCreate(&c->stream), "cudaStreamCreate");
+  c->own_stream = true;
+  return HLBM_OK;
+}
+
+void drop_graphs(hlbm_ctx* c) {
+  for (int k = 0; k < 2; ++k)
+    if (c->graph[k]) {
+      cudaGraphExecDestroy(c->graph[k]);
+      c->graph[k] = nullptr;
+    }
+}
+
+StepArgs make_args(const hlbm_ctx* c) {
+  StepArgs a{};
+  a.N = c->N;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.force_mode = c->force_mode;
+  a.gfield = c->gfield;
+  a.isothermal = (c->p.flags & HLBM_ISOTHERMAL) ? 1 : 0;
+  a.rho0 = (float)c->p.rho0;
+  a.omega = (float)(1.0 / c->tau_hat);
+  a.beta = (float)(1.0 - 0.5 / c->tau_hat);
+  for (int d = 0; d < 3; ++d) a.g[d] = (float)c->p.force[d];
+  a.h_coef = (c->p.flags & HLBM_SRC_H) ? (float)(1.0 - 1.0 / c->p.Pr) : 0.f;
+  a.eos = c->p.eos;
+  a.eos_a = (float)c->p.eos_a;
+  a.eos_b = (float)c->p.eos_b;
+  a.eos_T = (float)c->p.eos_T;
+  const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
+  // sigma = -k c0^2 |F^SC|^2 / (D tau G psi^2), tau = tau^ - 1/2, G = -1 (Eq. 3.12, Table 2)
+  a.p_coef = (c->p.flags & HLBM_SRC_P) ? (float)(c->p.k * cs2 / (c->D * (c->tau_hat - 0.5))) : 0.f;
+  return a;
+}
+
+cudaError_t launch_step(const hlbm_ctx* c, const StepArgs& a, bool moments) {
+  return c->lattice == 0 ? launch_step_d2q37(a, c->kind, c->storage, moments, c->rows, c->stream)
+                         : launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->stream);
+}
+
+cudaError_t one_step(hlbm_ctx* c) {
+  StepArgs a = make_args(c);
+  a.fin = c->pop[c->cur];
+  a.fout = c->pop[c->cur ^ 1];
+  cudaError_t e = launch_step(c, a, false);
+  c->cur ^= 1;
+  return e;
+}
+
+hlbm_status usable(hlbm_ctx* c) {
+  if (!c) return HLBM_EINVAL;
+  if (c->failed) return HLBM_ESTATE;
+  return HLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hlbm_workspace_bytes(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) {
+  std::string why;
+  if (validate(lattice, nx, ny, nz, 1.0, p, why) != HLBM_OK) return 0;
+  return layout(lattice, nx, ny, nz, p).total;
+}
+
+hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat, const hlbm_source_params* p,
+                        hlbm_ctx** out) {
+  if (!out) return HLBM_EINVAL;
+  *out = nullptr;
+  std::string why;
+  hlbm_status st = validate(lattice, nx, ny, nz, tau_hat, p, why);
+  if (st != HLBM_OK) {
+    std::fprintf(stderr, "hlbm_create: %s\n", why.c_str());
+    return st;
+  }
+  hlbm_ctx* c = new (std::nothrow) hlbm_ctx();
+  if (!c) return HLBM_ENOMEM;
+  c->lattice = lattice;
+  c->D = lattice == 0 ? 2 : 3;
+  c->Q = lattice == 0 ? 37 : 39;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->N = (long long)nx * ny * nz;
+  c->tau_hat = tau_hat;
+  c->p = *p;
+  c->storage = p->storage;
+  c->elem = p->storage == HLBM_F32 ? 4 : 2;
+  c->kind = (p->flags & HLBM_SRC_SC) ? KIND_SC : (p->flags & HLBM_SRC_H) ? KIND_THERMAL : KIND_LOCAL;
+  c->force_mode = (p->flags & HLBM_SRC_FORCE) ? FORCE_UNIFORM : FORCE_NONE;
+  c->rows = 8;
+  *out = c;
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_bind_memory(hlbm_ctx* c, void* dev_ptr, size_t bytes) {
+  if (!c || !dev_ptr) return HLBM_EINVAL;
+  if (c->arena) return fail(c, HLBM_ESTATE, "memory already allocated or bound");
+  if ((reinterpret_cast<uintptr_t>(dev_ptr) & 255) != 0) return fail(c, HLBM_EINVAL, "memory must be 256-byte aligned");
+  const Layout L = layout(c->lattice, c->nx, c->ny, c->nz, &c->p);
+  if (bytes < L.total) return fail(c, HLBM_ENOMEM, "bound memory smaller than hlbm_workspace_bytes()");
+  c->arena = static_cast<char*>(dev_ptr);
+  c->arena_bytes = bytes;
+  c->own_arena = false;
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_set_stream(hlbm_ctx* c, void* s) {
+  if (!c) return HLBM_EINVAL;
+  drop_graphs(c);
+  if (c->own_stream && c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+  }
+  c->own_stream = false;
+  c->stream = static_cast<cudaStream_t>(s);
+  return HLBM_OK;
+}
+
+void* hlbm_get_stream(hlbm_ctx* c) {
+  if (!c || ensure_stream(c) != HLBM_OK) return nullptr;
+  return c->stream;
+}
+
+hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float* theta, int on_device) {
+  if (!c || !rho || !u || !theta) return HLBM_EINVAL;
+  hlbm_status st = ensure_memory(c);
+  if (st != HLBM_OK) return st;
+  if ((st = ensure_stream(c)) != HLBM_OK) return st;
+  carve(c);
+  InitArgs a{};
+  a.N = c->N;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.rho0 = (float)c->p.rho0;
+  a.fout = c->pop[0];
+  if (on_device) {
+    a.rho = rho;
+    a.u = u;
+    a.theta = theta;
+  } else {
+    // stage the host fields in the second population buffer (the init
+    // kernel writes only the first); (D + 2) N floats always fit in Q N elements
+    const size_t n = (size_t)c->N;
+    float* stage = static_cast<float*>(c->pop[1]);
+    HLBM_CUDA(c, cudaMemcpyAsync(stage, rho, n * 4, cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+    HLBM_CUDA(c, cudaMemcpyAsync(stage + n, u, c->D * n * 4, cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+    HLBM_CUDA(c, cudaMemcpyAsync(stage + (1 + c->D) * n, theta, n * 4, cudaMemcpyHostToDevice, c->stream),
+              "cudaMemcpyAsync");
+    a.rho = stage;
+    a.u = stage + n;
+    a.theta = stage + (1 + c->D) * n;
+  }
+  cudaError_t e = launch_init(c->lattice, a, c->storage, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);  // host buffers are borrowed
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  c->cur = 0;
+  c->steps = 0;
+  c->initialised = true;
+  c->failed = false;
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_set_force_field(hlbm_ctx* c, const float* g, int kind, int on_device) {
+  hlbm_status st = usable(c);
+  if (st != HLBM_OK) return st;
+  if (!(c->p.flags & HLBM_SRC_FORCE)) return fail(c, HLBM_EINVAL, "context was created without HLBM_SRC_FORCE");
+  if (kind == 0) {
+    c->force_mode = FORCE_UNIFORM;
+    drop_graphs(c);
+    return HLBM_OK;
+  }
+  if ((kind != 1 && kind != 2) || !g) return fail(c, HLBM_EINVAL, "kind must be 0, 1 or 2 with a field pointer");
+  if ((st = ensure_memory(c)) != HLBM_OK) return st;
+  if ((st = ensure_stream(c)) != HLBM_OK) return st;
+  carve(c);
+  const size_t n = (kind == 1) ? (size_t)c->D * (size_t)c->N : (size_t)c->D * (size_t)c->ny;
+  HLBM_CUDA(c, cudaMemcpyAsync(c->gfield, g, n * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               c->stream), "cudaMemcpyAsync");
+  if (!on_device) HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  c->force_mode = (kind == 1) ? FORCE_FIELD : FORCE_PROFILE_Y;
+  drop_graphs(c);
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_step(hlbm_ctx* c, int n) {
+  hlbm_status st = usable(c);
+  if (st != HLBM_OK) return st;
+  if (n < 0) return fail(c, HLBM_EINVAL, "n must be >= 0");
+  if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
+  while (n >= kGraphSteps) {
+    cudaGraphExec_t& ge = c->graph[c->cur];
+    if (!ge) {
+      const int cur0 = c->cur;
+      HLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+      cudaError_t le = cudaSuccess;
+      for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) le = one_step(c);
+      cudaGraph_t gr = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &gr);
+      c->cur = cur0;
+      if (le != cudaSuccess) return cuda_fail(c, le, "step kernel (capture)");
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+      cudaError_t ie = cudaGraphInstantiate(&ge, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) {
+        ge = nullptr;
+        return cuda_fail(c, ie, "cudaGraphInstantiate");
+      }
+    }
+    HLBM_CUDA(c, cudaGraphLaunch(ge, c->stream), "cudaGraphLaunch");
+    n -= kGraphSteps;
+    c->steps += kGraphSteps;
+  }
+  for (int k = 0; k < n; ++k) {
+    cudaError_t e = one_step(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    c->steps += 1;
+  }
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on_device) {
+  hlbm_status st = usable(c);
+  if (st != HLBM_OK) return st;
+  if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
+  StepArgs a = make_args(c);
+  a.fin = c->pop[c->cur];
+  const size_t n = (size_t)c->N;
+  float* stage = nullptr;
+  if (on_device) {
+    a.rho_out = rho;
+    a.u_out = u;
+    a.theta_out = theta;
+  } else {
+    // stage in the population buffer that does not hold the current state
+    stage = static_cast<float*>(c->pop[c->cur ^ 1]);
+    a.rho_out = stage;
+    a.u_out = stage + n;
+    a.theta_out = stage + (1 + c->D) * n;
+  }
+  cudaError_t e = launch_step(c, a, true);
+  if (e == cudaSuccess && !on_device) {
+    if (rho) e = cudaMemcpyAsync(rho, stage, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, stage + n, c->D * n * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && theta)
+      e = cudaMemcpyAsync(theta, stage + (1 + c->D) * n, n * 4, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "moments");
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
+  hlbm_status st = usable(c);
+  if (st != HLBM_OK) return st;
+  if (!out) return HLBM_EINVAL;
+  if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
+  StepArgs a = make_args(c);
+  a.fin = c->pop[c->cur];
+  a.partials = c->partials;
+  HLBM_CUDA(c, launch_step(c, a, true), "moments kernel");
+  const int nb = moment_blocks(c->lattice, c->nx, c->ny, c->nz);
+  HLBM_CUDA(c, launch_reduce_partials(c->partials, nb, c->red, c->stream), "reduce kernel");
+  double s[8];
+  HLBM_CUDA(c, cudaMemcpyAsync(s, c->red, sizeof(s), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
+  const double Nn = (double)c->N;
+  out[0] = Nn * c->p.rho0 + s[0];
+  for (int d = 0; d < c->D; ++d) out[1 + d] = s[1 + d];
+  out[1 + c->D] = 0.5 * Nn * c->p.rho0 * c->D * cs2 + s[4];
+  if (s[5] > 0.0) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "diverged: %.0f nodes with non-finite moments or rho <= 0", s[5]);
+    return fail(c, HLBM_EDIVERGED, buf, true);
+  }
+  return HLBM_OK;
+}
+
+size_t hlbm_state_bytes(const hlbm_ctx* c) {
+  if (!c) return 0;
+  return 64 + (size_t)c->Q * (size_t)c->N * c->elem;
+}
+
+hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
+  hlbm_status st = usable(c);
+  if (st != HLBM_OK) return st;
+  if (!host_buf || bytes < hlbm_state_bytes(c)) return fail(c, HLBM_EINVAL, "buffer too small");
+  if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
+  long long hdr[8] = {0x484c424d31LL, c->lattice, c->nx, c->ny, c->nz, c->storage, c->steps, 0};
+  std::memcpy(host_buf, hdr, sizeof(hdr));
+  HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64, c->pop[c->cur], (size_t)c->Q * c->N * c->elem,
+                               cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return HLBM_EINVAL;
+  if (bytes < hlbm_state_bytes(c)) return fail(c, HLBM_EINVAL, "buffer too small");
+  long long hdr[8];
+  std::memcpy(hdr, host_buf, sizeof(hdr));
+  if (hdr[0] != 0x484c424d31LL || hdr[1] != c->lattice || hdr[2] != c->nx || hdr[3] != c->ny || hdr[4] != c->nz ||
+      hdr[5] != c->storage)
+    return fail(c, HLBM_EINVAL, "checkpoint does not match this context");
+  c->failed = false;
+  hlbm_status st = ensure_memory(c);
+  if (st != HLBM_OK) return st;
+  if ((st = ensure_stream(c)) != HLBM_OK) return st;
+  carve(c);
+  HLBM_CUDA(c, cudaMemcpyAsync(c->pop[0], static_cast<const char*>(host_buf) + 64, (size_t)c->Q * c->N * c->elem,
+                               cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  c->cur = 0;
+  c->steps = hdr[6];
+  c->initialised = true;
+  return HLBM_OK;
+}
+
+long long hlbm_step_count(const hlbm_ctx* c) { return c ? c->steps : -1; }
+
+hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows) {
+  if (!c) return HLBM_EINVAL;
+  if (rows == 0) rows = 8;
+  if (rows != 4 && rows != 8 && rows != 16) return fail(c, HLBM_EINVAL, "rows must be 4, 8 or 16");
+  if (c->lattice == 1 && rows == 16) return fail(c, HLBM_EINVAL, "D3Q39 tiles have 4 or 8 rows");
+  c->rows = rows;
+  drop_graphs(c);
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_synchronize(hlbm_ctx* c) {
+  if (!c) return HLBM_EINVAL;
+  if (!c->stream) return HLBM_OK;
+  HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return HLBM_OK;
+}
+
+const char* hlbm_last_error(const hlbm_ctx* c) { return c ? c->msg.c_str() : "null context"; }
+
+hlbm_status hlbm_destroy(hlbm_ctx* c) {
+  if (!c) return HLBM_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->own_arena && c->arena) cudaFree(c->arena);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return HLBM_OK;
+}
+
+int hlbm_lattice_info(int lattice, int* cvec, double* w, double* cs2) {
+  if (lattice == HLBM_D2Q37) {
+    for (int i = 0; i < 37; ++i) {
+      if (cvec)
+        for (int a = 0; a < 3; ++a) cvec[3 * i + a] = D2Q37::c(i, a);
+      if (w) w[i] = D2Q37::w(i);
+    }
+    if (cs2) *cs2 = D2Q37::cs2;
+    return 37;
+  }
+  if (lattice == HLBM_D3Q39) {
+    for (int i = 0; i < 39; ++i) {
+      if (cvec)
+        for (int a = 0; a < 3; ++a) cvec[3 * i + a] = D3Q39::c(i, a);
+      if (w) w[i] = D3Q39::w(i);
+    }
+    if (cs2) *cs2 = D3Q39::cs2;
+    return 39;
+  }
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Kernel argument blocks and launcher declarations shared by the CUDA
+// translation units of libhlbm (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace hlbm {
+
+enum Kind : int {
+  KIND_LOCAL = 0,    // sources need only the node itself (F_i)
+  KIND_THERMAL = 1,  // + H_i: theta of the 2D / 3D nearest neighbours
+  KIND_SC = 2        // + F^SC (and P_i): psi of the reach-3 neighbourhood
+};
+enum Storage : int { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+enum ForceMode : int { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2, FORCE_PROFILE_Y = 3 };
+
+// Arguments of the fused step / moments kernels (passed as a grid constant).
+struct StepArgs {
+  const void* fin;        // populations at time t (post-collision state of t-1), [Q][N]
+  void* fout;             // populations written by this step, [Q][N]
+  const float* gfield;    // FORCE_FIELD: [D][N]; FORCE_PROFILE_Y: [D][ny]
+  float* rho_out;         // moments mode outputs (may be null)
+  float* u_out;
+  float* theta_out;
+  double* partials;       // moments mode: per-block FP64 sums [blocks][8] (may be null)
+  long long N;            // nodes
+  int nx, ny, nz;
+  int force_mode;
+  int isothermal;
+  float rho0;
+  float omega;            // 1 / tau^
+  float beta;             // 1 - 1 / (2 tau^)
+  float g[3];             // uniform acceleration
+  float h_coef;           // 1 - 1/Pr (H_i)
+  int eos;                // 0 van der Waals, 1 Carnahan-Starling
+  float eos_a, eos_b, eos_T;
+  float p_coef;           // trace coefficient of P_i: sigma = p_coef |F^SC|^2 / psi^2
+};
+
+// Arguments of the initialisation kernel.
+struct InitArgs {
+  const float* rho;
+  const float* u;
+  const float* theta;
+  void* fout;
+  long long N;
+  int nx, ny, nz;
+  float rho0;
+};
+
+// Launchers (return the launch error).  rows: tile rows per CTA (4, 8, 16).
+cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool moments, int rows,
+                              cudaStream_t s);
+cudaError_t launch_step_d3q39(const StepArgs& a, int kind, int storage, bool moments, int rows,
+                              cudaStream_t s);
+cudaError_t launch_init(int lattice, const InitArgs& a, int storage, cudaStream_t s);
+// Sums per-block partials into out[0..7] (FP64) and the non-finite counter.
+cudaError_t launch_reduce_partials(const double* partials, int blocks, double* out, cudaStream_t s);
+// Number of CTAs a moments-mode launch with these sizes uses (size of the partials).
+int moment_blocks(int lattice, int nx, int ny, int nz);
+
+}  // namespace hlbm

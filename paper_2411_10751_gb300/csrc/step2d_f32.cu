@@ -1,0 +1,8 @@
+// D2Q37 fused step kernels with f32 population storage.
+#include "step2d.cuh"
+
+namespace hlbm {
+cudaError_t launch_step2d_f32(const StepArgs& a, int kind, bool mom, int rows, cudaStream_t s) {
+  return launch_step2d_st<ST_F32>(a, kind, mom, rows, s);
+}
+}  // namespace hlbm

@@ -1,0 +1,8 @@
+// D3Q39 fused step kernels with bf16 population storage.
+#include "step3d.cuh"
+
+namespace hlbm {
+cudaError_t launch_step3d_bf16(const StepArgs& a, int kind, bool mom, int rows, cudaStream_t s) {
+  return launch_step3d_st<ST_BF16>(a, kind, mom, rows, s);
+}
+}  // namespace hlbm

@@ -1,0 +1,8 @@
+// D3Q39 fused step kernels with f16 population storage.
+#include "step3d.cuh"
+
+namespace hlbm {
+cudaError_t launch_step3d_f16(const StepArgs& a, int kind, bool mom, int rows, cudaStream_t s) {
+  return launch_step3d_st<ST_F16>(a, kind, mom, rows, s);
+}
+}  // namespace hlbm

@@ -1,0 +1,167 @@
+"""Python front end of the hlbm C ABI: one object per context.
+
+Device memory comes from PyTorch (the context's workspace is a torch uint8
+tensor bound with hlbm_bind_memory) and work is ordered on a CUDA stream;
+all computation happens in libhlbm's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import abi
+
+LATTICES = {"D2Q37": abi.HLBM_D2Q37, "D3Q39": abi.HLBM_D3Q39}
+STORAGE = {"f32": abi.HLBM_F32, "f16": abi.HLBM_F16, "bf16": abi.HLBM_BF16}
+FORCE_KIND = {None: 0, "field": 1, "profile": 2}
+
+
+def make_params(params: dict, storage: str = "f32") -> abi.hlbm_source_params:
+    """hlbm_source_params from a parameter dict (keys as in workloads.source_params)."""
+    p = abi.hlbm_source_params()
+    flags = 0
+    if params.get("force"):
+        flags |= abi.HLBM_SRC_FORCE
+    if params.get("H"):
+        flags |= abi.HLBM_SRC_H
+    if params.get("SC"):
+        flags |= abi.HLBM_SRC_SC
+    if params.get("P"):
+        flags |= abi.HLBM_SRC_P
+    if params.get("isothermal"):
+        flags |= abi.HLBM_ISOTHERMAL
+    p.flags = flags
+    g = list(params.get("g", (0.0, 0.0, 0.0))) + [0.0, 0.0, 0.0]
+    for a in range(3):
+        p.force[a] = float(g[a])
+    p.Pr = float(params.get("Pr", 1.0))
+    p.eos = {"vdw": 0, "cs": 1}[params.get("eos", "vdw")]
+    p.eos_a = float(params.get("eos_a", 0.0))
+    p.eos_b = float(params.get("eos_b", 0.0))
+    p.eos_T = float(params.get("eos_T", 0.0))
+    p.k = float(params.get("k", 0.0))
+    p.rho0 = float(params.get("rho0", 1.0))
+    p.storage = STORAGE[storage]
+    return p
+
+
+def _dev_f32(x, device) -> torch.Tensor:
+    t = torch.as_tensor(x, dtype=torch.float32, device=device)
+    return t.contiguous()
+
+
+class HLBM:
+    """A periodic D2Q37 / D3Q39 domain advanced by the fused GPU step."""
+
+    def __init__(self, lattice: str, nx: int, ny: int, nz: int, tau_hat: float, params: dict,
+                 storage: str = "f32", device: int | str | torch.device = 0, stream: torch.cuda.Stream | None = None):
+        self.lattice, self.nx, self.ny, self.nz = lattice, nx, ny, max(1, nz)
+        self.D = 2 if lattice == "D2Q37" else 3
+        self.N = nx * ny * self.nz
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.storage = storage
+        self._p = make_params(params, storage)
+        ctx = C.c_void_p()
+        abi.check(abi.hlbm_create(LATTICES[lattice], nx, ny, self.nz, float(tau_hat), C.byref(self._p), C.byref(ctx)))
+        self.ctx = ctx
+        nbytes = abi.hlbm_workspace_bytes(LATTICES[lattice], nx, ny, self.nz, C.byref(self._p))
+        with torch.cuda.device(self.device):
+            self._arena = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            s = stream if stream is not None else torch.cuda.current_stream(self.device)
+            abi.check(abi.hlbm_set_stream(self.ctx, C.c_void_p(s.cuda_stream)), self.ctx)
+        abi.check(abi.hlbm_bind_memory(self.ctx, C.c_void_p(self._arena.data_ptr()), nbytes), self.ctx)
+
+    # ------------------------------------------------------------ helpers
+    @property
+    def shape(self):
+        return (self.ny, self.nx) if self.D == 2 else (self.nz, self.ny, self.nx)
+
+    def cuda_stream(self) -> torch.cuda.ExternalStream:
+        """The stream the context's kernels run on (for events and ordering)."""
+        h = abi.hlbm_get_stream(self.ctx)
+        return torch.cuda.ExternalStream(h, device=self.device)
+
+    def _chk(self, st):
+        abi.check(st, self.ctx)
+
+    # --------------------------------------------------------------- API
+    def init(self, rho, u, theta) -> None:
+        """f^ = f^eq(rho, u, theta); torch CUDA tensors stay on the device, anything else is copied from host."""
+        if all(isinstance(t, torch.Tensor) and t.is_cuda for t in (rho, u, theta)):
+            r, uu, th = (_dev_f32(t, self.device) for t in (rho, u, theta))
+            self._chk(abi.hlbm_init(self.ctx, r.data_ptr(), uu.data_ptr(), th.data_ptr(), 1))
+            self.synchronize()
+        else:
+            r, uu, th = (np.ascontiguousarray(np.asarray(t, dtype=np.float32)) for t in (rho, u, theta))
+            self._chk(abi.hlbm_init(self.ctx, r.ctypes.data, uu.ctypes.data, th.ctypes.data, 0))
+
+    def set_force_field(self, g, kind: str | None = "field") -> None:
+        """Acceleration field: kind 'field' [D, ...], 'profile' [D, ny], or None (uniform params['g'])."""
+        if kind is None:
+            self._chk(abi.hlbm_set_force_field(self.ctx, None, 0, 0))
+            return
+        if isinstance(g, torch.Tensor) and g.is_cuda:
+            t = _dev_f32(g, self.device)
+            self._chk(abi.hlbm_set_force_field(self.ctx, t.data_ptr(), FORCE_KIND[kind], 1))
+            self.synchronize()
+        else:
+            a = np.ascontiguousarray(np.asarray(g, dtype=np.float32))
+            self._chk(abi.hlbm_set_force_field(self.ctx, a.ctypes.data, FORCE_KIND[kind], 0))
+
+    def step(self, n: int = 1) -> None:
+        self._chk(abi.hlbm_step(self.ctx, int(n)))
+
+    def moments(self):
+        """(rho, u, theta) as torch float32 CUDA tensors (ordered on the context's stream)."""
+        rho = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        u = torch.empty((self.D,) + self.shape, dtype=torch.float32, device=self.device)
+        th = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._chk(abi.hlbm_moments(self.ctx, rho.data_ptr(), u.data_ptr(), th.data_ptr(), 1))
+        self.synchronize()
+        return rho, u, th
+
+    def moments_host(self):
+        """(rho, u, theta) as numpy float32 arrays."""
+        rho = np.empty(self.shape, np.float32)
+        u = np.empty((self.D,) + self.shape, np.float32)
+        th = np.empty(self.shape, np.float32)
+        self._chk(abi.hlbm_moments(self.ctx, rho.ctypes.data, u.ctypes.data, th.ctypes.data, 0))
+        return rho, u, th
+
+    def diag(self) -> np.ndarray:
+        out = (C.c_double * 5)()
+        self._chk(abi.hlbm_diag(self.ctx, out))
+        return np.array(out[: self.D + 2])
+
+    def save(self) -> bytes:
+        n = abi.hlbm_state_bytes(self.ctx)
+        buf = C.create_string_buffer(n)
+        self._chk(abi.hlbm_save(self.ctx, buf, n))
+        return buf.raw
+
+    def load(self, state: bytes) -> None:
+        self._chk(abi.hlbm_load(self.ctx, state, len(state)))
+
+    @property
+    def step_count(self) -> int:
+        return int(abi.hlbm_step_count(self.ctx))
+
+    def set_tile(self, rows: int) -> None:
+        self._chk(abi.hlbm_set_tile(self.ctx, int(rows)))
+
+    def synchronize(self) -> None:
+        self._chk(abi.hlbm_synchronize(self.ctx))
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            abi.hlbm_destroy(self.ctx)
+            self.ctx = None
+            self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA fused step (through the C ABI) against the FP64 oracle.
+
+Metric (per field q in rho, u, theta): max over nodes of |q_gpu - q_oracle|
+divided by max |q_oracle| (|.| the vector norm for u).  Bar for FP32
+storage: 1e-5 after 100 steps.  Reduced-precision storage: max|u - u_oracle|
+/ max|u| <= 1e-3 (FP16).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.solver import Oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def HLBM():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2411_10751_gb300 as pkg
+    pkg.build()
+    from paper_2411_10751_gb300.solver import HLBM as cls
+    return cls
+
+
+def rel_err(m_gpu, m_ora):
+    rho, u, th = m_gpu
+    r0, u0, t0 = m_ora
+    er = np.abs(rho - r0).max() / np.abs(r0).max()
+    eu = np.sqrt(((u - u0) ** 2).sum(0)).max() / max(np.sqrt((u0 ** 2).sum(0)).max(), 1e-300)
+    et = np.abs(th - t0).max() / np.abs(t0).max()
+    return er, eu, et
+
+
+def run_pair(HLBM, case, steps, storage="f32", rows=None, force_kind="field"):
+    g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage)
+    if rows:
+        g.set_tile(rows)
+    o = Oracle(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params)
+    if case.gfield is not None:
+        o.set_force_field(case.gfield)
+        if force_kind == "profile":
+            g.set_force_field(case.gfield[:, :, 0] if case.D == 2 else case.gfield[:, 0, :, 0], "profile")
+        else:
+            g.set_force_field(case.gfield, "field")
+    g.init(case.rho, case.u, case.theta)
+    o.init(case.rho, case.u, case.theta)
+    g.step(steps)
+    o.run(steps)
+    mg = g.moments_host()
+    mo = o.moments()
+    g.close()
+    return mg, mo
+
+
+def test_kolmogorov_64_parity_and_profile(HLBM):
+    c = W.kolmogorov(64)
+    mg, mo = run_pair(HLBM, c, 100)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
+def test_kolmogorov_64_2000_steps(HLBM):
+    from oracle import analytic, lattice
+    c = W.kolmogorov(64)
+    mg, mo = run_pair(HLBM, c, 2000, force_kind="profile")
+    assert max(rel_err(mg, mo)) < 1e-4, rel_err(mg, mo)
+    nu = analytic.viscosity(lattice.d2q37().cs2, c.tau_hat)
+    ua = analytic.kolmogorov_ux(np.arange(64), 2000, c.meta["g0"], nu, 64)
+    assert np.abs(mg[1][0] - ua[:, None]).max() / np.abs(ua).max() < 1e-2
+
+
+@pytest.mark.parametrize("nx,ny", [(7, 7), (45, 37), (100, 75)])
+def test_thermal_parity_ragged(HLBM, nx, ny):
+    c = W.thermal_decay(nx=nx, ny=ny, tau_hat=0.7, Pr=0.71)
+    mg, mo = run_pair(HLBM, c, 100)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
+@pytest.mark.parametrize("rows", [4, 8, 16])
+def test_thermal_tile_rows(HLBM, rows):
+    c = W.thermal_decay(nx=70, ny=53, tau_hat=0.7, Pr=0.71)
+    mg, mo = run_pair(HLBM, c, 30, rows=rows)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
+def test_thermal_1024_full_size(HLBM):
+    """The benchmark workload at its full size, in the benchmark's launch configuration."""
+    c = W.thermal_decay(n=1024)
+    mg, mo = run_pair(HLBM, c, 100)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
+@pytest.mark.parametrize("k", [0.01, 1.5672])
+def test_droplet_parity_small(HLBM, k):
+    c = W.droplet(nx=70, ny=53, r0=14.0, k=k)
+    mg, mo = run_pair(HLBM, c, 100)
+    er, eu, et = rel_err(mg, mo)
+    assert er < TOL32 and et < TOL32 and eu < TOL32, (er, eu, et)
+
+
+def test_droplet_512_full_size(HLBM):
+    c = W.droplet(n=512)
+    mg, mo = run_pair(HLBM, c, 100)
+    er, eu, et = rel_err(mg, mo)
+    assert er < TOL32 and et < TOL32 and eu < TOL32, (er, eu, et)
+
+
+def test_d3q39_taylor_green_parity(HLBM):
+    c = W.taylor_green_3d(n=16, tau_hat=0.6, Ma=0.3)
+    rng = np.random.default_rng(0)
+    c.gfield = 1e-5 * (2 * rng.random(c.gfield.shape) - 1)
+    mg, mo = run_pair(HLBM, c, 50)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
+def test_d3q39_ragged_uniform_force(HLBM):
+    c = W.taylor_green_3d(n=16, tau_hat=0.7, Ma=0.1)
+    # ragged non-cubic box: crop the fields
+    sl = (slice(0, 9), slice(0, 11), slice(0, 37 % 16 + 16))
+    c.rho, c.theta = c.rho[sl].copy(), c.theta[sl].copy()
+    c.u = c.u[(slice(None),) + sl].copy()
+    c.nz, c.ny, c.nx = c.rho.shape
+    c.gfield = None
+    c.params["g"] = (1e-5, -2e-5, 3e-5)
+    mg, mo = run_pair(HLBM, c, 40)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
+@pytest.mark.parametrize("storage,tol_u", [("f16", 1e-3), ("bf16", 2e-2)])
+def test_reduced_precision_storage(HLBM, storage, tol_u):
+    c = W.thermal_decay(nx=128, ny=128, tau_hat=0.7, Pr=0.71)
+    mg, mo = run_pair(HLBM, c, 100, storage=storage)
+    er, eu, et = rel_err(mg, mo)
+    assert eu < tol_u, (storage, er, eu, et)
+
+
+def test_force_profile_equals_full_field_bitwise(HLBM):
+    c = W.kolmogorov(64, nx=40, ny=50)
+    a, _ = run_pair(HLBM, c, 30, force_kind="field")
+    b, _ = run_pair(HLBM, c, 30, force_kind="profile")
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_graph_replay_equals_single_steps_bitwise(HLBM):
+    c = W.thermal_decay(nx=48, ny=40, tau_hat=0.7, Pr=0.71)
+    g1 = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    g2 = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    g1.init(c.rho, c.u, c.theta)
+    g2.init(c.rho, c.u, c.theta)
+    g1.step(70)                      # two graph replays of 32 steps + 6 single steps
+    for _ in range(70):
+        g2.step(1)
+    for x, y in zip(g1.moments_host(), g2.moments_host()):
+        assert np.array_equal(x, y)
+    assert g1.step_count == g2.step_count == 70
+
+
+def test_save_load_resume_bitwise(HLBM):
+    c = W.droplet(nx=48, ny=40, r0=10.0, k=1.0)
+    g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    g.init(c.rho, c.u, c.theta)
+    g.step(100)
+    ref = g.moments_host()
+    g.init(c.rho, c.u, c.theta)
+    g.step(60)
+    state = g.save()
+    g2 = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    g2.load(state)
+    assert g2.step_count == 60
+    g2.step(40)
+    for x, y in zip(ref, g2.moments_host()):
+        assert np.array_equal(x, y)
+
+
+def test_fp64_diagnostics_conservation(HLBM):
+    rho = 1.0 + 0.02 * np.sin(2 * np.pi * np.arange(40) / 40)[None, :] * np.ones((36, 1))
+    u = np.zeros((2, 36, 40))
+    u[0] = 0.01 * np.cos(2 * np.pi * np.arange(36) / 36)[:, None]
+    th = 1.0 + 0.01 * np.cos(2 * np.pi * np.arange(40) / 40)[None, :] * np.ones((36, 1))
+    p = W.source_params(H=True, Pr=0.71)
+    g = HLBM("D2Q37", 40, 36, 1, 0.7, p)
+    o = Oracle("D2Q37", 40, 36, 1, 0.7, p)
+    g.init(rho, u, th)
+    o.init(rho, u, th)
+    d0 = g.diag()
+    g.step(500)
+    o.run(500)
+    d1 = g.diag()
+    do = o.diag()
+    assert abs(d1[0] - d0[0]) < 1e-6 * d0[0]               # FP32 storage, FP64 sums
+    assert np.abs(d1[1:3] - d0[1:3]).max() < 1e-6 * d0[0]
+    assert abs(d1[3] - d0[3]) < 1e-6 * d0[3]
+    assert np.abs(d1 - do).max() < 1e-5 * np.abs(do).max()
+
+
+def test_divergence_is_detected_and_sticky(HLBM):
+    from paper_2411_10751_gb300 import abi
+    c = W.thermal_decay(nx=32, ny=32)
+    rho = c.rho.copy()
+    rho[5, 7] = -1.0                 # unphysical density: must be reported, not hidden
+    g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    g.init(rho, c.u, c.theta)
+    g.step(2)
+    with pytest.raises(abi.HLBMError) as e:
+        g.diag()
+    assert e.value.status == abi.HLBM_EDIVERGED
+    with pytest.raises(abi.HLBMError) as e2:
+        g.step(1)
+    assert e2.value.status == abi.HLBM_ESTATE
+    g.init(c.rho, c.u, c.theta)      # a fresh init clears the error state
+    g.step(1)
+    assert np.isfinite(g.diag()).all()
+
+
+def test_zero_steps_is_identity(HLBM):
+    c = W.kolmogorov(16)
+    g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    g.init(c.rho, c.u, c.theta)
+    a = g.moments_host()
+    g.step(0)
+    b = g.moments_host()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert np.abs(a[0] - 1.0).max() < 1e-7
