@@ -142,12 +142,21 @@ hlbm_status hlbm_load(hlbm_ctx* ctx, const void* host_buf, size_t bytes);
 /* Steps taken since hlbm_init / hlbm_load. */
 long long hlbm_step_count(const hlbm_ctx* ctx);
 
-/* Tile rows per CTA of the fused step (2D: 4, 8 or 16; 0 = default).  Used by
- * the autotuner; results do not depend on it. */
-hlbm_status hlbm_set_tile(hlbm_ctx* ctx, int rows);
+/* Schedule of the fused step: tile rows per CTA (2D: 4, 8 or 16; D3Q39: 4
+ * or 8; 0 = default 8) and nodes per thread (1, or 2 on paired FP32 lanes
+ * with 8 or 16 rows; 0 = default 2; D2Q37 only).  Chosen by the autotuner;
+ * results agree to rounding across schedules. */
+hlbm_status hlbm_set_tile(hlbm_ctx* ctx, int rows, int nodes_per_thread);
 
-/* Waits for all work on the context's stream. */
+/* Waits for all work on the context's stream.  Returns HLBM_ETIMEOUT (and
+ * enters the error state) if a kernel reported an expired bounded wait. */
 hlbm_status hlbm_synchronize(hlbm_ctx* ctx);
+
+/* Wall-time limit of each bounded device-side wait (the mbarrier wait of
+ * the TMA staging), in seconds, 0 < seconds <= 60; default 2.  A kernel
+ * whose wait expires skips its tile, sets a status word, and the next
+ * hlbm_synchronize / hlbm_moments / hlbm_diag returns HLBM_ETIMEOUT. */
+hlbm_status hlbm_set_wait_timeout(hlbm_ctx* ctx, double seconds);
 
 /* Message of the last failing call on this context (never NULL). */
 const char* hlbm_last_error(const hlbm_ctx* ctx);

@@ -24,7 +24,7 @@ for _k, _v in STATUS.items():
 # every symbol include/hlbm.h declares
 EXPORTS = ["hlbm_workspace_bytes", "hlbm_create", "hlbm_bind_memory", "hlbm_set_stream", "hlbm_get_stream",
            "hlbm_init", "hlbm_set_force_field", "hlbm_step", "hlbm_moments", "hlbm_diag", "hlbm_state_bytes",
-           "hlbm_save", "hlbm_load", "hlbm_step_count", "hlbm_set_tile", "hlbm_synchronize",
+           "hlbm_save", "hlbm_load", "hlbm_step_count", "hlbm_set_tile", "hlbm_synchronize", "hlbm_set_wait_timeout",
            "hlbm_last_error", "hlbm_destroy", "hlbm_lattice_info"]
 
 
@@ -63,8 +63,9 @@ _sigs = {
     "hlbm_save": ([_vp, _vp, _sz], _i),
     "hlbm_load": ([_vp, _vp, _sz], _i),
     "hlbm_step_count": ([_vp], _ll),
-    "hlbm_set_tile": ([_vp, _i], _i),
+    "hlbm_set_tile": ([_vp, _i, _i], _i),
     "hlbm_synchronize": ([_vp], _i),
+    "hlbm_set_wait_timeout": ([_vp, _d], _i),
     "hlbm_last_error": ([_vp], C.c_char_p),
     "hlbm_destroy": ([_vp], _i),
     "hlbm_lattice_info": ([_i, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)], _i),

@@ -1,11 +1,14 @@
 // Host implementation of the hlbm C ABI (include/hlbm.h): validation,
 // device memory (own allocation or a caller-bound arena), stream ordering,
 // CUDA-graph replay of the step loop, diagnostics and checkpoints.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "hlbm.h"
 #include "internal.h"
@@ -23,6 +26,7 @@ struct hlbm_ctx {
   int storage = ST_F32;
   size_t elem = 4;
   int rows = 8;
+  int npt = 2;
 
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -45,6 +49,18 @@ struct hlbm_ctx {
 
   // graphs replaying kGraphSteps steps from buffer parity 0 / 1
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+  // TMA staging of interior tiles (D2Q37): tensor maps per (buffer, box)
+  bool tma_ok = false;
+  bool tma_store_ok = false;
+  struct TMap {
+    int buf, wb, hb;
+    CUtensorMap map;
+  };
+  std::vector<TMap> tmaps;
+  int* status = nullptr;          // device status word (bounded waits)
+  unsigned long long wait_ns = 2000000000ull;
+  int debug_skip_tma = 0;
 };
 
 static const int kGraphSteps = 32;  // even: a replay returns to the same buffer parity
@@ -154,6 +170,7 @@ void carve(hlbm_ctx* c) {
   c->gfield = (c->p.flags & HLBM_SRC_FORCE) ? reinterpret_cast<float*>(c->arena + L.off_g) : nullptr;
   c->partials = reinterpret_cast<double*>(c->arena + L.off_part);
   c->red = reinterpret_cast<double*>(c->arena + L.off_red);
+  c->status = reinterpret_cast<int*>(c->arena + L.off_red + 64);
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -189,15 +206,86 @@ StepArgs make_args(const hlbm_ctx* c) {
   a.eos_a = (float)c->p.eos_a;
   a.eos_b = (float)c->p.eos_b;
   a.eos_T = (float)c->p.eos_T;
+  a.status = c->status;
+  a.tma = c->tma_ok ? 1 : 0;
+  a.wait_ns = c->wait_ns;
+  a.debug_skip_tma = c->debug_skip_tma;
   const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
   // sigma = -k c0^2 |F^SC|^2 / (D tau G psi^2), tau = tau^ - 1/2, G = -1 (Eq. 3.12, Table 2)
   a.p_coef = (c->p.flags & HLBM_SRC_P) ? (float)(c->p.k * cs2 / (c->D * (c->tau_hat - 0.5))) : 0.f;
   return a;
 }
 
-cudaError_t launch_step(const hlbm_ctx* c, const StepArgs& a, bool moments) {
-  return c->lattice == 0 ? launch_step_d2q37(a, c->kind, c->storage, moments, c->rows, c->stream)
-                         : launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->stream);
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of population buffer `buf` viewed as [Q][ny][nx] with a
+// wb x hb x 1 box; null if it cannot be encoded (the kernel then stages
+// every tile with plain loads).
+const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
+  for (auto& t : c->tmaps)
+    if (t.buf == buf && t.wb == wb && t.hb == hb) return &t.map;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return nullptr;
+  hlbm_ctx::TMap t{};
+  t.buf = buf;
+  t.wb = wb;
+  t.hb = hb;
+  const CUtensorMapDataType dt = c->storage == ST_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : c->storage == ST_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->Q};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->nx * c->elem, (cuuint64_t)c->N * c->elem};
+  const cuuint32_t box[3] = {(cuuint32_t)wb, (cuuint32_t)hb, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&t.map, dt, 3, c->pop[buf], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return nullptr;
+  c->tmaps.push_back(t);
+  return &c->tmaps.back().map;
+}
+
+cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
+  if (c->lattice != 0) return launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->stream);
+  CUtensorMap maps[2];
+  std::memset(maps, 0, sizeof(maps));
+  a.tma_store = 0;
+  if (a.tma) {
+    int wb = 0, hb = 0, ob = 0;
+    step_box_d2q37(c->kind, c->storage, moments, c->rows, &wb, &hb, &ob);
+    const int buf = (a.fin == c->pop[0]) ? 0 : 1;
+    const CUtensorMap* in = tensor_map(c, buf, wb, hb);
+    const CUtensorMap* out = moments ? nullptr : tensor_map(c, buf ^ 1, 32, ob);
+    if (in) maps[0] = *in;
+    else a.tma = 0;
+    if (out && c->tma_store_ok) {
+      maps[1] = *out;
+      a.tma_store = 1;
+    }
+  }
+  return launch_step_d2q37(a, c->kind, c->storage, moments, c->rows, c->npt, maps, c->stream);
+}
+
+// HLBM_ETIMEOUT if a kernel reported an expired bounded wait (synchronises).
+hlbm_status check_status(hlbm_ctx* c) {
+  int st = 0;
+  HLBM_CUDA(c, cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st == HLBM_ETIMEOUT) return fail(c, HLBM_ETIMEOUT, "a bounded device wait expired (TMA staging)", true);
+  return HLBM_OK;
 }
 
 cudaError_t one_step(hlbm_ctx* c) {
@@ -251,6 +339,13 @@ hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat, con
   c->kind = (p->flags & HLBM_SRC_SC) ? KIND_SC : (p->flags & HLBM_SRC_H) ? KIND_THERMAL : KIND_LOCAL;
   c->force_mode = (p->flags & HLBM_SRC_FORCE) ? FORCE_UNIFORM : FORCE_NONE;
   c->rows = 8;
+  // TMA needs a row pitch that is a multiple of 16 bytes
+  const char* no_tma = std::getenv("HLBM_NO_TMA");
+  c->tma_ok = lattice == HLBM_D2Q37 && ((size_t)nx * c->elem) % 16 == 0 && !(no_tma && no_tma[0] == '1');
+  const char* no_tma_st = std::getenv("HLBM_NO_TMA_STORE");
+  c->tma_store_ok = c->tma_ok && !(no_tma_st && no_tma_st[0] == '1');
+  const char* skip = std::getenv("HLBM_TEST_SKIP_TMA");
+  c->debug_skip_tma = (skip && skip[0] == '1') ? 1 : 0;
   *out = c;
   return HLBM_OK;
 }
@@ -290,6 +385,7 @@ hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float
   if (st != HLBM_OK) return st;
   if ((st = ensure_stream(c)) != HLBM_OK) return st;
   carve(c);
+  if (c->lattice == 0) HLBM_CUDA(c, configure_step_d2q37(c->storage), "cudaFuncSetAttribute");
   InitArgs a{};
   a.N = c->N;
   a.nx = c->nx;
@@ -314,7 +410,8 @@ hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float
     a.u = stage + n;
     a.theta = stage + (1 + c->D) * n;
   }
-  cudaError_t e = launch_init(c->lattice, a, c->storage, c->stream);
+  cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = launch_init(c->lattice, a, c->storage, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);  // host buffers are borrowed
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   c->cur = 0;
@@ -411,7 +508,7 @@ hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "moments");
-  return HLBM_OK;
+  return on_device ? HLBM_OK : check_status(c);
 }
 
 hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
@@ -427,7 +524,7 @@ hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
   HLBM_CUDA(c, launch_reduce_partials(c->partials, nb, c->red, c->stream), "reduce kernel");
   double s[8];
   HLBM_CUDA(c, cudaMemcpyAsync(s, c->red, sizeof(s), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
-  HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if ((st = check_status(c)) != HLBM_OK) return st;
   const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
   const double Nn = (double)c->N;
   out[0] = Nn * c->p.rho0 + s[0];
@@ -472,8 +569,10 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
   if (st != HLBM_OK) return st;
   if ((st = ensure_stream(c)) != HLBM_OK) return st;
   carve(c);
+  if (c->lattice == 0) HLBM_CUDA(c, configure_step_d2q37(c->storage), "cudaFuncSetAttribute");
   HLBM_CUDA(c, cudaMemcpyAsync(c->pop[0], static_cast<const char*>(host_buf) + 64, (size_t)c->Q * c->N * c->elem,
                                cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  HLBM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   c->cur = 0;
   c->steps = hdr[6];
@@ -483,12 +582,16 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
 
 long long hlbm_step_count(const hlbm_ctx* c) { return c ? c->steps : -1; }
 
-hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows) {
+hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread) {
   if (!c) return HLBM_EINVAL;
   if (rows == 0) rows = 8;
+  if (nodes_per_thread == 0) nodes_per_thread = 2;
   if (rows != 4 && rows != 8 && rows != 16) return fail(c, HLBM_EINVAL, "rows must be 4, 8 or 16");
+  if (nodes_per_thread != 1 && nodes_per_thread != 2) return fail(c, HLBM_EINVAL, "nodes_per_thread must be 1 or 2");
+  if (nodes_per_thread == 2 && rows == 4) return fail(c, HLBM_EINVAL, "two nodes per thread need 8 or 16 rows");
   if (c->lattice == 1 && rows == 16) return fail(c, HLBM_EINVAL, "D3Q39 tiles have 4 or 8 rows");
   c->rows = rows;
+  c->npt = nodes_per_thread;
   drop_graphs(c);
   return HLBM_OK;
 }
@@ -497,6 +600,14 @@ hlbm_status hlbm_synchronize(hlbm_ctx* c) {
   if (!c) return HLBM_EINVAL;
   if (!c->stream) return HLBM_OK;
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (c->status && c->initialised) return check_status(c);
+  return HLBM_OK;
+}
+
+hlbm_status hlbm_set_wait_timeout(hlbm_ctx* c, double seconds) {
+  if (!c || !std::isfinite(seconds) || !(seconds > 0) || seconds > 60) return HLBM_EINVAL;
+  c->wait_ns = (unsigned long long)(seconds * 1e9);
+  drop_graphs(c);
   return HLBM_OK;
 }
 

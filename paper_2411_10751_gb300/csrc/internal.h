@@ -2,6 +2,7 @@
 // translation units of libhlbm (not part of the public C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -36,6 +37,11 @@ struct StepArgs {
   int eos;                // 0 van der Waals, 1 Carnahan-Starling
   float eos_a, eos_b, eos_T;
   float p_coef;           // trace coefficient of P_i: sigma = p_coef |F^SC|^2 / psi^2
+  int* status;            // device status word: set to HLBM_ETIMEOUT when a bounded wait expires
+  int tma;                // 1: interior tiles are staged by TMA (input tensor map valid)
+  int tma_store;          // 1: results are written by TMA (output tensor map valid)
+  unsigned long long wait_ns;  // wall-time limit of a bounded mbarrier wait
+  int debug_skip_tma;     // test hook: arm the barrier but issue no copy (the wait must expire)
 };
 
 // Arguments of the initialisation kernel.
@@ -49,11 +55,20 @@ struct InitArgs {
   float rho0;
 };
 
-// Launchers (return the launch error).  rows: tile rows per CTA (4, 8, 16).
-cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool moments, int rows,
-                              cudaStream_t s);
+// Launchers (return the launch error).  rows: tile rows per CTA (4, 8, 16);
+// tmap: {input map, output map} of the population buffers with the boxes of
+// step_box_d2q37 (may be null when a.tma == 0 and a.tma_store == 0).
+// npt: nodes per thread (1, or 2 on float2 lanes; 8- and 16-row tiles).
+cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool moments, int rows, int npt,
+                              const CUtensorMap* tmap, cudaStream_t s);
 cudaError_t launch_step_d3q39(const StepArgs& a, int kind, int storage, bool moments, int rows,
                               cudaStream_t s);
+// Sets the dynamic shared-memory limit of every D2Q37 kernel of a storage type
+// (call before the first launch, outside stream capture).
+cudaError_t configure_step_d2q37(int storage);
+// TMA boxes that launch_step_d2q37 expects: input box wb x hb, output tile
+// 32 x ob.
+void step_box_d2q37(int kind, int storage, bool moments, int rows, int* wb, int* hb, int* ob);
 cudaError_t launch_init(int lattice, const InitArgs& a, int storage, cudaStream_t s);
 // Sums per-block partials into out[0..7] (FP64) and the non-finite counter.
 cudaError_t launch_reduce_partials(const double* partials, int blocks, double* out, cudaStream_t s);

@@ -5,20 +5,46 @@
 
 namespace hlbm {
 
-cudaError_t launch_step2d_f32(const StepArgs&, int, bool, int, cudaStream_t);
-cudaError_t launch_step2d_f16(const StepArgs&, int, bool, int, cudaStream_t);
-cudaError_t launch_step2d_bf16(const StepArgs&, int, bool, int, cudaStream_t);
+cudaError_t launch_step2d_f32(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
+cudaError_t launch_step2d_f16(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
+cudaError_t launch_step2d_bf16(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
+cudaError_t configure_step2d_f32();
+cudaError_t configure_step2d_f16();
+cudaError_t configure_step2d_bf16();
+void box_step2d_f32(int, bool, int, int*, int*, int*);
+void box_step2d_f16(int, bool, int, int*, int*, int*);
+void box_step2d_bf16(int, bool, int, int*, int*, int*);
 cudaError_t launch_step3d_f32(const StepArgs&, int, bool, int, cudaStream_t);
 cudaError_t launch_step3d_f16(const StepArgs&, int, bool, int, cudaStream_t);
 cudaError_t launch_step3d_bf16(const StepArgs&, int, bool, int, cudaStream_t);
 
-cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool mom, int rows, cudaStream_t s) {
+cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool mom, int rows, int npt,
+                              const CUtensorMap* tm, cudaStream_t s) {
   switch (storage) {
-    case ST_F32: return launch_step2d_f32(a, kind, mom, rows, s);
-    case ST_F16: return launch_step2d_f16(a, kind, mom, rows, s);
-    case ST_BF16: return launch_step2d_bf16(a, kind, mom, rows, s);
+    case ST_F32: return launch_step2d_f32(a, kind, mom, rows, npt, tm, s);
+    case ST_F16: return launch_step2d_f16(a, kind, mom, rows, npt, tm, s);
+    case ST_BF16: return launch_step2d_bf16(a, kind, mom, rows, npt, tm, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t configure_step_d2q37(int storage) {
+  static bool done[3] = {false, false, false};
+  if (storage < 0 || storage > 2) return cudaErrorInvalidValue;
+  if (done[storage]) return cudaSuccess;
+  cudaError_t e = storage == ST_F32   ? configure_step2d_f32()
+                  : storage == ST_F16 ? configure_step2d_f16()
+                                      : configure_step2d_bf16();
+  if (e == cudaSuccess) done[storage] = true;
+  return e;
+}
+
+void step_box_d2q37(int kind, int storage, bool mom, int rows, int* wb, int* hb, int* ob) {
+  switch (storage) {
+    case ST_F32: box_step2d_f32(kind, mom, rows, wb, hb, ob); return;
+    case ST_F16: box_step2d_f16(kind, mom, rows, wb, hb, ob); return;
+    default: box_step2d_bf16(kind, mom, rows, wb, hb, ob); return;
+  }
 }
 
 cudaError_t launch_step_d3q39(const StepArgs& a, int kind, int storage, bool mom, int rows, cudaStream_t s) {

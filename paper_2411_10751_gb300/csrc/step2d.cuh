@@ -1,35 +1,61 @@
-// Fused pull-collide-source step on D2Q37 (Eq. 4.4), one node per thread.
+// Fused pull-collide-source step on D2Q37 (Eq. 4.4), one node per thread,
+// with the pulled populations staged in shared memory by TMA.
 //
-// CTA tile: 32 x BY nodes (a warp spans 32 consecutive x, so every pulled
-// load and every store of a warp covers one contiguous row segment).
-// Population planes are [Q][ny][nx] (structure of arrays), periodic by index
-// wrap with no halo cells in memory.
+// CTA tile: 32 x BY nodes; population planes are [Q][ny][nx] in global
+// memory (structure of arrays, periodic by index wrap, no halo cells).
+// A node x pulls g_i from x - c_i.  For the tile and a frame of H nodes
+// around it (the "region", (32 + 2H) x (BY + 2H) nodes), plane i is needed on
+// the region shifted by -c_i; that rectangle, widened on the left to the
+// 16-byte x alignment of tiled bulk copies and to a common width WB, is one
+// TMA box.  One thread issues the Q boxes against an mbarrier; every gather is
+// then a shared-memory load at a compile-time offset.  The left widening of
+// plane i, rem_i = (-H - c_ix) mod A (A = 16 bytes / element), does not depend
+// on the tile because tile x origins are multiples of 32.
+// Tiles whose boxes would cross the periodic edge (or domains whose row pitch
+// is not a multiple of 16 bytes) fill the same layout with wrapped loads.
 //
-// Neighbour fields of time t (no lag, as the sources of Eq. 4.4 are all taken
-// at time t):
-//   KIND_THERMAL  grad theta for H_i needs theta at the four nearest
-//                 neighbours: each CTA recomputes theta on a one-node frame
-//                 around its tile from pulled populations into shared memory.
-//   KIND_SC       F^SC (Eq. 3.8) needs psi(rho) on the reach-3 neighbourhood:
-//                 psi on a three-node frame is recomputed the same way.
-// The frame's populations come mostly from L2 (neighbouring CTAs read them
-// too), so HBM traffic stays one read and one write of every population.
-//
-// Threads whose node lies past the domain edge (ragged last tile) compute the
-// aux value of the periodic image of their position so that the shared tile
-// is exact, and skip the store.
+// Neighbour fields of time t (no lag: all sources of Eq. 4.4 are taken at t):
+//   KIND_THERMAL  grad theta for H_i: theta on the 4-neighbour ring (H = 1)
+//   KIND_SC       F^SC (Eq. 3.8): psi(rho) on a three-node frame (H = 3)
+// Both are computed from the staged populations of the region into a
+// shared-memory tile, so the frame costs arithmetic but no extra HBM reads.
 #pragma once
 
 #include "step_common.cuh"
+#include "tma.cuh"
+
+#include <type_traits>
 
 namespace hlbm {
+
+template <int ST, int KIND, bool MOM, int BY>
+struct Cfg2 {
+  using C = Codec<ST>;
+  using T = typename C::T;
+  using L = D2Q37;
+  static constexpr int BX = 32;
+  static constexpr int NT = BX * BY;
+  static constexpr int H = (KIND == KIND_SC) ? 3 : ((KIND == KIND_THERMAL && !MOM) ? 1 : 0);
+  static constexpr int A = 16 / (int)sizeof(T);
+  static constexpr int RW = BX + 2 * H, RH = BY + 2 * H;
+  static constexpr int WB = ((RW + A - 1 + A - 1) / A) * A;  // box width (elements)
+  static constexpr int HB = RH;                             // box height
+  static constexpr int PLANE_BYTES = ((WB * HB * (int)sizeof(T) + 127) / 128) * 128;
+  static constexpr int PLANE = PLANE_BYTES / (int)sizeof(T);
+  static constexpr int POP_BYTES = L::Q * PLANE_BYTES;
+  static constexpr int AUX_BYTES = (H > 0) ? ((RW * RH * 4 + 127) / 128) * 128 : 0;
+  static constexpr int RED_BYTES = MOM ? ((NT / 32) * 6 * 8 + 127) / 128 * 128 : 0;
+  static constexpr int SMEM = POP_BYTES + AUX_BYTES + RED_BYTES + 128;  // + mbarrier
+  static constexpr uint32_t TX_BYTES = (uint32_t)L::Q * WB * HB * (uint32_t)sizeof(T);
+  __host__ __device__ static constexpr int rem(int i) { return ((-H - L::c(i, 0)) % A + A) % A; }
+};
 
 template <int BX, int BY, int H>
 struct Frame2 {
   static constexpr int SW = BX + 2 * H;
   static constexpr int SH = BY + 2 * H;
-  // nodes on the frame around the tile: the 4-neighbour ring for H == 1
-  // (no corners), the full ring for H == 3
+  // region nodes outside the tile: the 4-neighbour ring for H == 1 (no
+  // corners), the full frame for H == 3
   static constexpr int count = (H == 1) ? 2 * BX + 2 * BY : SW * SH - BX * BY;
   __device__ static __forceinline__ void pos(int k, int& i, int& j) {
     if constexpr (H == 1) {
@@ -50,111 +76,216 @@ struct Frame2 {
   }
 };
 
-// theta - 1 of a node from its pulled populations (Eq. 4.5), local force only
-template <class L>
-__device__ __forceinline__ float theta_bar_local(const StepArgs& a, const float (&g)[L::Q], int node, int y) {
-  float dr, J[3], Pi;
-  moments<L>(g, dr, J, Pi);
-  const float rho = a.rho0 + dr;
-  float acc[3];
-  accel<2>(a, node, y, acc);
-  const float inv = 1.f / rho;
-  const float ux = fmaf(0.5f * rho, acc[0], J[0]) * inv;
-  const float uy = fmaf(0.5f * rho, acc[1], J[1]) * inv;
-  const float G2 = 2.f * rho * (ux * acc[0] + uy * acc[1]);
-  constexpr float Dc = (float)(2.0 * L::cs2);
-  return (Pi - dr * Dc - rho * (ux * ux + uy * uy) + 0.5f * G2) * inv * (1.f / Dc);
+// the Q pulled populations of region node (rx, ry) from the staged planes
+template <class Cf>
+__device__ __forceinline__ void load_region(const typename Cf::T* sp, int rx, int ry, float (&g)[37]) {
+  const int base = ry * Cf::WB + rx;
+  static_for<37>([&](auto I) {
+    constexpr int i = I;
+    g[i] = to_float(sp[i * Cf::PLANE + base + Cf::rem(i)]);
+  });
 }
 
-template <int ST, int KIND, bool MOM, int BY>
-__global__ void __launch_bounds__(32 * BY, (BY <= 8) ? 2 : 1) step2d_kernel(const __grid_constant__ StepArgs a) {
+// theta - 1 of a node from its pulled populations (Eq. 4.5), local force only
+template <class L>
+__device__ __forceinline__ float theta_bar_local(const StepArgs& a, float (&g)[L::Q], int node, int y) {
+  float dr, acc, J[3], Pih;
+  moments_h<L>(g, dr, acc, J, Pih);
+  const float rho = a.rho0 + dr;
+  float gacc[3];
+  accel<2>(a, node, y, gacc);
+  const float inv = 1.f / rho;
+  const float ux = fmaf(0.5f * rho, gacc[0], J[0]) * inv;
+  const float uy = fmaf(0.5f * rho, gacc[1], J[1]) * inv;
+  const float G2 = 2.f * rho * (ux * gacc[0] + uy * gacc[1]);
+  constexpr float Dc = (float)(2.0 * L::cs2);
+  return (Pih - rho * (ux * ux + uy * uy) + 0.5f * G2) * inv * (1.f / Dc);
+}
+
+// CTAs per SM the register budget is sized for: as many as the staged tile's
+// shared memory allows, at most 3 for 256 threads (80 registers), 2 for 512.
+template <int ST, int KIND, bool MOM, int BY, int NPT>
+constexpr int min_ctas2() {
+  constexpr int threads = 32 * BY / NPT;
+  constexpr int by_smem = (227 * 1024) / Cfg2<ST, KIND, MOM, BY>::SMEM;
+  constexpr int cap = (threads >= 512) ? 2 : (threads <= 128 ? 4 : 3);
+  return by_smem < 1 ? 1 : (by_smem < cap ? by_smem : cap);
+}
+
+// NPT nodes per thread: thread (tx, ty) owns tile rows ty + k * BY / NPT,
+// k < NPT; with NPT = 2 the node arithmetic runs on float2 lanes.
+template <int ST, int KIND, bool MOM, int BY, int NPT>
+__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, NPT>()))
+    step2d_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap,
+                  const __grid_constant__ CUtensorMap tmap_out) {
+  using Cf = Cfg2<ST, KIND, MOM, BY>;
   using L = D2Q37;
-  using C = Codec<ST>;
-  using T = typename C::T;
-  constexpr int BX = 32;
-  constexpr int NT = BX * BY;
-  constexpr int H = (KIND == KIND_SC) ? 3 : ((KIND == KIND_THERMAL && !MOM) ? 1 : 0);
+  using T = typename Cf::T;
+  using V = typename std::conditional<NPT == 2, float2, float>::type;
+  constexpr int BX = Cf::BX, H = Cf::H;
+  constexpr int TR = BY / NPT;     // thread rows
+  constexpr int NT = BX * TR;      // threads
   using Fr = Frame2<BX, BY, (H > 0 ? H : 1)>;
   constexpr float Dc = (float)(2.0 * L::cs2);
   constexpr float inv_c0 = (float)(1.0 / L::c0);
-  __shared__ float aux[(H > 0) ? Fr::SW * Fr::SH : 1];
-  __shared__ double red[MOM ? (NT / 32) * 6 : 1];
 
-  const T* __restrict__ fin = static_cast<const T*>(a.fin);
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* sp = reinterpret_cast<T*>(smem);
+  float* aux = reinterpret_cast<float*>(smem + Cf::POP_BYTES);
+  double* red = reinterpret_cast<double*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
+
   const int nx = a.nx, ny = a.ny;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const int gxp = x0 + tx, gyp = y0 + ty;
-  const bool active = gxp < nx && gyp < ny;
-  const int x = gxp < nx ? gxp : gxp % nx;
-  const int y = gyp < ny ? gyp : gyp % ny;
-  const int node = y * nx + x;
 
-  float g[L::Q];
-  gather<L, C>(fin, a.N, nx, ny, 1, x, y, 0, g);
-  float dr, J[3], Pi;
-  moments<L>(g, dr, J, Pi);
-  const float rho = a.rho0 + dr;
-  float acc[3];
-  accel<2>(a, node, y, acc);
-  float Fx = rho * acc[0], Fy = rho * acc[1];
-  float sigma = 0.f;
+  // ---- stage the region's pulled populations
+  const bool boxed = a.tma && (x0 - H - 3 - (Cf::A - 1) >= 0) && (x0 - H + 3 + Cf::WB <= nx) &&
+                     (y0 - H - 3 >= 0) && (y0 - H + 3 + Cf::HB <= ny) && ((smem_u32(smem) & 127u) == 0);
+  if (boxed) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, Cf::TX_BYTES);
+      if (!a.debug_skip_tma) {
+        static_for<37>([&](auto I) {
+          constexpr int i = I;
+          tma_load_3d(sp + i * Cf::PLANE, &tmap, x0 - H - L::c(i, 0) - Cf::rem(i), y0 - H - L::c(i, 1), i, bar);
+        });
+      }
+    }
+    bool ok = mbar_wait_bounded(bar, 0, a.wait_ns);
+    if (!__syncthreads_and(ok)) {
+      // copies did not complete: report, give in-flight copies a second bounded
+      // wait, and leave without touching the outputs
+      if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
+      mbar_wait_bounded(bar, 0, a.wait_ns);
+      __syncthreads();
+      return;
+    }
+  } else {
+    // edge tile: every region node gathers its Q pulled populations with
+    // periodic wrap (independent loads) and writes them into the staged layout
+    const T* __restrict__ fin = static_cast<const T*>(a.fin);
+    for (int k = tid; k < Cf::RW * Cf::RH; k += NT) {
+      const int ry = k / Cf::RW, rx = k - ry * Cf::RW;
+      const int X = wrapm(x0 - H + rx, nx), Y = wrapm(y0 - H + ry, ny);
+      float gk[37];
+      gather<L, typename Cf::C>(fin, a.N, nx, ny, 1, X, Y, 0, gk);
+      const int base = ry * Cf::WB + rx;
+      static_for<37>([&](auto I) {
+        constexpr int i = I;
+        sp[i * Cf::PLANE + base + Cf::rem(i)] = from_float<T>(gk[i]);
+      });
+    }
+    __syncthreads();
+  }
+
+  // ---- this thread's nodes (lane k: tile row ty + k * TR)
+  const int x = (x0 + tx < nx) ? x0 + tx : (x0 + tx) % nx;
+  int yk[NPT], nodek[NPT];
+  bool activek[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    const int gyp = y0 + ty + k * TR;
+    activek[k] = (x0 + tx < nx) && gyp < ny;
+    yk[k] = gyp < ny ? gyp : gyp % ny;
+    nodek[k] = yk[k] * nx + x;
+  }
+
+  V g[37];
+  static_for<37>([&](auto I) {
+    constexpr int i = I;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k)
+      set_lane(g[i], k, to_float(sp[i * Cf::PLANE + (ty + k * TR + H) * Cf::WB + tx + H + Cf::rem(i)]));
+  });
+  V dr, acc, J[3], Pih;
+  moments_h<L>(g, dr, acc, J, Pih);
+  const V rho = vadd(splat<V>(a.rho0), dr);
+  V gax = splat<V>(0.f), gay = splat<V>(0.f);
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    float ga[3];
+    accel<2>(a, nodek[k], yk[k], ga);
+    set_lane(gax, k, ga[0]);
+    set_lane(gay, k, ga[1]);
+  }
+  V Fx = vmul(rho, gax), Fy = vmul(rho, gay);
+  V sigma = splat<V>(0.f);
 
   if constexpr (KIND == KIND_SC) {
-    const float psi = psi_of<L>(a, rho);
-    aux[(ty + H) * Fr::SW + tx + H] = psi;
+    const V psi = vmap(rho, [&](float r) { return psi_of<L>(a, r); });
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) aux[(ty + k * TR + H) * Fr::SW + tx + H] = lane(psi, k);
     for (int k = tid; k < Fr::count; k += NT) {
       int i, j;
       Fr::pos(k, i, j);
-      const int hx = wrapm(x0 - H + i, nx), hy = wrapm(y0 - H + j, ny);
-      float gh[L::Q];
-      gather<L, C>(fin, a.N, nx, ny, 1, hx, hy, 0, gh);
-      aux[j * Fr::SW + i] = psi_of<L>(a, a.rho0 + sum_w<L>(gh));
+      float gh[37];
+      static_for<37>([&](auto I) {
+        constexpr int q = I;
+        gh[q] = to_float(sp[q * Cf::PLANE + j * Cf::WB + i + Cf::rem(q)]);
+      });
+      aux[j * Fr::SW + i] = psi_of<L>(a, a.rho0 + density_h<L>(gh));
     }
     __syncthreads();
     // F^SC = -G psi(x) sum_i w_i psi(x + c_i) c_i with G = -1
-    float sx = 0.f, sy = 0.f;
+    V sx = splat<V>(0.f), sy = splat<V>(0.f);
     static_for<L::NPAIR>([&](auto P) {
       constexpr int i = 2 * P + 1;
       constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
-      const float dpsi = aux[(ty + H + cy) * Fr::SW + tx + H + cx] - aux[(ty + H - cy) * Fr::SW + tx + H - cx];
-      if constexpr (cx != 0) sx = fmaf((float)(L::w(i) * cx), dpsi, sx);
-      if constexpr (cy != 0) sy = fmaf((float)(L::w(i) * cy), dpsi, sy);
+      V dpsi;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int r = ty + k * TR + H;
+        set_lane(dpsi, k, aux[(r + cy) * Fr::SW + tx + H + cx] - aux[(r - cy) * Fr::SW + tx + H - cx]);
+      }
+      if constexpr (cx != 0) sx = vfma(splat<V>((float)(L::w(i) * cx)), dpsi, sx);
+      if constexpr (cy != 0) sy = vfma(splat<V>((float)(L::w(i) * cy)), dpsi, sy);
     });
-    const float fsx = psi * sx, fsy = psi * sy;
-    Fx += fsx;
-    Fy += fsy;
+    const V fsx = vmul(psi, sx), fsy = vmul(psi, sy);
+    Fx = vadd(Fx, fsx);
+    Fy = vadd(Fy, fsy);
     // P_i trace coefficient (Eq. 3.12): sigma = p_coef |F^SC|^2 / psi^2
-    sigma = (psi > 0.f) ? a.p_coef * (fsx * fsx + fsy * fsy) / (psi * psi) : 0.f;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      const float ps = lane(psi, k), fx = lane(fsx, k), fy = lane(fsy, k);
+      set_lane(sigma, k, (ps > 0.f) ? a.p_coef * (fx * fx + fy * fy) / (ps * ps) : 0.f);
+    }
   }
 
-  const float inv_rho = 1.f / rho;
-  const float ux = fmaf(0.5f, Fx, J[0]) * inv_rho;
-  const float uy = fmaf(0.5f, Fy, J[1]) * inv_rho;
-  const float uu = ux * ux + uy * uy;
-  const float G2 = 2.f * (ux * Fx + uy * Fy) + Dc * sigma;
-  const float tb_m = (Pi - dr * Dc - rho * uu + 0.5f * G2) * inv_rho * (1.f / Dc);
+  const V inv_rho = vmap(rho, [](float r) { return 1.f / r; });
+  const V ux = vmul(vfma(splat<V>(0.5f), Fx, J[0]), inv_rho);
+  const V uy = vmul(vfma(splat<V>(0.5f), Fy, J[1]), inv_rho);
+  const V uu = vfma(ux, ux, vmul(uy, uy));
+  const V G2 = vfma(splat<V>(Dc), sigma, vmul(splat<V>(2.f), vfma(ux, Fx, vmul(uy, Fy))));
+  const V tb_m = vmul(vmul(vfma(splat<V>(0.5f), G2, vsub(Pih, vmul(rho, uu))), inv_rho), splat<V>(1.f / Dc));
 
   if constexpr (MOM) {
-    if (active) {
-      if (a.rho_out) a.rho_out[node] = rho;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if (!activek[k]) continue;
+      const int node = nodek[k];
+      const float r = lane(rho, k), vx = lane(ux, k), vy = lane(uy, k), tb = lane(tb_m, k);
+      if (a.rho_out) a.rho_out[node] = r;
       if (a.u_out) {
-        a.u_out[node] = ux;
-        a.u_out[(size_t)a.N + node] = uy;
+        a.u_out[node] = vx;
+        a.u_out[(size_t)a.N + node] = vy;
       }
-      if (a.theta_out) a.theta_out[node] = 1.f + tb_m;
+      if (a.theta_out) a.theta_out[node] = 1.f + tb;
+      // FP64 block sums: d rho, rho u, (Pi + G2/2)/2, non-finite count
+      const bool bad = !(isfinite(r) && r > 0.f && isfinite(vx) && isfinite(vy) && isfinite(tb));
+      v[0] += lane(dr, k);
+      v[1] += (double)r * vx;
+      v[2] += (double)r * vy;
+      v[4] += 0.5 * ((double)lane(Pih, k) + (double)Dc * lane(dr, k) + 0.5 * (double)lane(G2, k));
+      v[5] += bad ? 1.0 : 0.0;
     }
     if (a.partials) {
-      // FP64 block sums: d rho, rho u, (Pi + G2/2)/2, non-finite count
-      double v[6] = {0, 0, 0, 0, 0, 0};
-      if (active) {
-        const bool bad = !(isfinite(rho) && rho > 0.f && isfinite(ux) && isfinite(uy) && isfinite(tb_m));
-        v[0] = dr;
-        v[1] = (double)rho * ux;
-        v[2] = (double)rho * uy;
-        v[4] = 0.5 * ((double)Pi + 0.5 * (double)G2);
-        v[5] = bad ? 1.0 : 0.0;
-      }
 #pragma unroll
       for (int k = 0; k < 6; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
@@ -163,81 +294,176 @@ __global__ void __launch_bounds__(32 * BY, (BY <= 8) ? 2 : 1) step2d_kernel(cons
         for (int k = 0; k < 6; ++k) red[(tid >> 5) * 6 + k] = v[k];
       __syncthreads();
       if (tid < 6) {
-        double s = 0.0;
-        for (int w = 0; w < NT / 32; ++w) s += red[w * 6 + tid];
-        a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + tid] = s;
+        double sum = 0.0;
+        for (int w = 0; w < NT / 32; ++w) sum += red[w * 6 + tid];
+        a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + tid] = sum;
       }
     }
   } else {
-    NodeSrc s;
-    s.hG[0] = s.hG[1] = s.hG[2] = 0.f;
+    NodeSrcT<V> s;
+    s.hG[0] = s.hG[1] = s.hG[2] = splat<V>(0.f);
     if constexpr (KIND == KIND_THERMAL) {
-      // theta - 1 on the tile and its 4-neighbour frame, then grad theta
-      aux[(ty + 1) * Fr::SW + tx + 1] = tb_m;
+      // theta - 1 on the tile and its 4-neighbour ring, then grad theta
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) aux[(ty + k * TR + 1) * Fr::SW + tx + 1] = lane(tb_m, k);
       for (int k = tid; k < Fr::count; k += NT) {
         int i, j;
         Fr::pos(k, i, j);
         const int hx = wrapm(x0 - 1 + i, nx), hy = wrapm(y0 - 1 + j, ny);
-        float gh[L::Q];
-        gather<L, C>(fin, a.N, nx, ny, 1, hx, hy, 0, gh);
+        float gh[37];
+        static_for<37>([&](auto I) {
+          constexpr int q = I;
+          gh[q] = to_float(sp[q * Cf::PLANE + j * Cf::WB + i + Cf::rem(q)]);
+        });
         aux[j * Fr::SW + i] = theta_bar_local<L>(a, gh, hy * nx + hx, hy);
       }
       __syncthreads();
-      const float gtx = 0.5f * (aux[(ty + 1) * Fr::SW + tx + 2] - aux[(ty + 1) * Fr::SW + tx]);
-      const float gty = 0.5f * (aux[(ty + 2) * Fr::SW + tx + 1] - aux[ty * Fr::SW + tx + 1]);
+      V gtx, gty;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int r = ty + k * TR + 1;
+        set_lane(gtx, k, 0.5f * (aux[r * Fr::SW + tx + 2] - aux[r * Fr::SW + tx]));
+        set_lane(gty, k, 0.5f * (aux[(r + 1) * Fr::SW + tx + 1] - aux[(r - 1) * Fr::SW + tx + 1]));
+      }
       // s^(3) += rho theta (1 - 1/Pr) [delta grad_xi theta], grad_xi = c0 grad
-      const float hc = rho * (1.f + tb_m) * a.h_coef * (float)L::c0;
-      s.hG[0] = hc * gtx;
-      s.hG[1] = hc * gty;
+      const V hc = vmul(vmul(rho, vadd(splat<V>(1.f), tb_m)), splat<V>(a.h_coef * (float)L::c0));
+      s.hG[0] = vmul(hc, gtx);
+      s.hG[1] = vmul(hc, gty);
     }
-    s.dr = dr;
+    s.dr = splat<V>(0.f);  // density deviation re-enters in apply_poly_h
     s.rho = rho;
-    s.tb = a.isothermal ? 0.f : tb_m;
-    s.u[0] = ux * inv_c0;
-    s.u[1] = uy * inv_c0;
-    s.u[2] = 0.f;
-    s.F[0] = Fx * inv_c0;
-    s.F[1] = Fy * inv_c0;
-    s.F[2] = 0.f;
+    s.tb = a.isothermal ? splat<V>(0.f) : tb_m;
+    s.u[0] = vmul(ux, splat<V>(inv_c0));
+    s.u[1] = vmul(uy, splat<V>(inv_c0));
+    s.u[2] = splat<V>(0.f);
+    s.F[0] = vmul(Fx, splat<V>(inv_c0));
+    s.F[1] = vmul(Fy, splat<V>(inv_c0));
+    s.F[2] = splat<V>(0.f);
     s.sigma = sigma;
-    float K[15];
+    V K[15];
     poly2<L>(s, a.omega, a.beta, K);
-    apply_poly<L, 15>(g, K, 1.f - a.omega);
-    if (active) {
-      T* __restrict__ fout = static_cast<T*>(a.fout);
-      static_for<L::Q>([&](auto I) {
+    const float om1 = 1.f - a.omega;
+    K[0] = vfma(splat<V>(-om1), acc, K[0]);
+    apply_poly_h<L, 15>(g, K, om1, dr);
+    if (a.tma_store) {
+      // stage the tile's results densely in the (now unused) input planes and
+      // write each plane with one bulk tensor store; out-of-domain rows and
+      // columns of a ragged tile are clipped by the copy
+      __syncthreads();
+      static_for<37>([&](auto I) {
         constexpr int i = I;
-        C::st(fout + (size_t)i * (size_t)a.N + node, g[i]);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) sp[i * Cf::PLANE + (ty + k * TR) * BX + tx] = from_float<T>(lane(g[i], k));
       });
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        static_for<37>([&](auto I) {
+          constexpr int i = I;
+          tma_store_3d(&tmap_out, sp + i * Cf::PLANE, x0, y0, i);
+        });
+        bulk_commit();
+        bulk_wait_all();
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        if (!activek[k]) continue;
+        T* __restrict__ fout = static_cast<T*>(a.fout) + nodek[k];
+        static_for<37>([&](auto I) {
+          constexpr int i = I;
+          Cf::C::st(fout + (size_t)i * (size_t)a.N, lane(g[i], k));
+        });
+      }
     }
   }
 }
 
-template <int ST>
-cudaError_t launch_step2d_st(const StepArgs& a, int kind, bool mom, int rows, cudaStream_t s) {
-  const int by = (rows == 4 || rows == 16) ? rows : 8;
-  const dim3 grid((a.nx + 31) / 32, (a.ny + by - 1) / by, 1);
-  const dim3 block(32, by, 1);
-#define HLBM_L2(K, M, R) step2d_kernel<ST, K, M, R><<<grid, block, 0, s>>>(a)
-  if (mom) {
-    const dim3 g8((a.nx + 31) / 32, (a.ny + 7) / 8, 1);
-    if (kind == KIND_SC) step2d_kernel<ST, KIND_SC, true, 8><<<g8, dim3(32, 8), 0, s>>>(a);
-    else step2d_kernel<ST, KIND_LOCAL, true, 8><<<g8, dim3(32, 8), 0, s>>>(a);
-  } else if (by == 4) {
-    if (kind == KIND_SC) HLBM_L2(KIND_SC, false, 4);
-    else if (kind == KIND_THERMAL) HLBM_L2(KIND_THERMAL, false, 4);
-    else HLBM_L2(KIND_LOCAL, false, 4);
-  } else if (by == 8) {
-    if (kind == KIND_SC) HLBM_L2(KIND_SC, false, 8);
-    else if (kind == KIND_THERMAL) HLBM_L2(KIND_THERMAL, false, 8);
-    else HLBM_L2(KIND_LOCAL, false, 8);
-  } else {
-    if (kind == KIND_SC) HLBM_L2(KIND_SC, false, 16);
-    else if (kind == KIND_THERMAL) HLBM_L2(KIND_THERMAL, false, 16);
-    else HLBM_L2(KIND_LOCAL, false, 16);
+// Box geometry of the launch configuration (for the host's tensor maps).
+template <int ST, int KIND, bool MOM, int BY>
+void box_of(int& wb, int& hb) {
+  wb = Cfg2<ST, KIND, MOM, BY>::WB;
+  hb = Cfg2<ST, KIND, MOM, BY>::HB;
+}
+template <int ST, int KIND, bool MOM, int BY>
+int rows_of() {
+  return BY;
+}
+
+template <int ST, int KIND, bool MOM, int BY, int NPT = 1>
+cudaError_t configure2() {
+  return cudaFuncSetAttribute(step2d_kernel<ST, KIND, MOM, BY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg2<ST, KIND, MOM, BY>::SMEM);
+}
+
+template <int ST, int KIND, bool MOM, int BY, int NPT = 1>
+cudaError_t launch2(const StepArgs& a, const CUtensorMap* tmaps, cudaStream_t s) {
+  using Cf = Cfg2<ST, KIND, MOM, BY>;
+  const dim3 grid((a.nx + 31) / 32, (a.ny + BY - 1) / BY, 1);
+  const dim3 block(32, BY / NPT, 1);
+  CUtensorMap tm{}, tmo{};
+  if (tmaps) {
+    tm = tmaps[0];
+    tmo = tmaps[1];
   }
-#undef HLBM_L2
+  step2d_kernel<ST, KIND, MOM, BY, NPT><<<grid, block, Cf::SMEM, s>>>(a, tm, tmo);
   return cudaGetLastError();
+}
+
+// Sets the shared-memory size attribute of every 2D kernel of this storage
+// (done once, outside any stream capture).
+template <int ST>
+cudaError_t configure_step2d_st() {
+  const cudaError_t es[] = {
+      configure2<ST, KIND_LOCAL, false, 4>(),   configure2<ST, KIND_THERMAL, false, 4>(),
+      configure2<ST, KIND_SC, false, 4>(),      configure2<ST, KIND_LOCAL, false, 8>(),
+      configure2<ST, KIND_THERMAL, false, 8>(), configure2<ST, KIND_SC, false, 8>(),
+      configure2<ST, KIND_LOCAL, false, 16>(),  configure2<ST, KIND_THERMAL, false, 16>(),
+      configure2<ST, KIND_SC, false, 16>(),     configure2<ST, KIND_LOCAL, true, 8>(),
+      configure2<ST, KIND_SC, true, 8>(),       configure2<ST, KIND_LOCAL, false, 8, 2>(),
+      configure2<ST, KIND_THERMAL, false, 8, 2>(), configure2<ST, KIND_SC, false, 8, 2>(),
+      configure2<ST, KIND_LOCAL, false, 16, 2>(), configure2<ST, KIND_THERMAL, false, 16, 2>(),
+      configure2<ST, KIND_SC, false, 16, 2>()};
+  for (cudaError_t e : es)
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Dispatch: box geometry query (wb/hb/ob non-null: input box and output
+// tile rows) or launch.  tm: {input map, output map} or null.
+template <int ST>
+cudaError_t launch_step2d_st(const StepArgs& a, int kind, bool mom, int rows, int npt, const CUtensorMap* tm,
+                             cudaStream_t s, int* wb, int* hb, int* ob = nullptr) {
+  const int by = (rows == 4 || rows == 16) ? rows : 8;
+  const int np = (npt == 2 && by >= 8 && !mom) ? 2 : 1;
+#define HLBM_CASE(K, M, R, NP)                    \
+  do {                                            \
+    if (wb) {                                     \
+      box_of<ST, K, M, R>(*wb, *hb);              \
+      if (ob) *ob = rows_of<ST, K, M, R>();       \
+      return cudaSuccess;                         \
+    }                                             \
+    return launch2<ST, K, M, R, NP>(a, tm, s);    \
+  } while (0)
+#define HLBM_KINDS(R, NP)                                      \
+  do {                                                         \
+    if (kind == KIND_SC) HLBM_CASE(KIND_SC, false, R, NP);     \
+    if (kind == KIND_THERMAL) HLBM_CASE(KIND_THERMAL, false, R, NP); \
+    HLBM_CASE(KIND_LOCAL, false, R, NP);                       \
+  } while (0)
+  if (mom) {
+    if (kind == KIND_SC) HLBM_CASE(KIND_SC, true, 8, 1);
+    HLBM_CASE(KIND_LOCAL, true, 8, 1);
+  }
+  if (by == 4) HLBM_KINDS(4, 1);
+  if (by == 8) {
+    if (np == 2) HLBM_KINDS(8, 2);
+    HLBM_KINDS(8, 1);
+  }
+  if (np == 2) HLBM_KINDS(16, 2);
+  HLBM_KINDS(16, 1);
+#undef HLBM_KINDS
+#undef HLBM_CASE
 }
 
 }  // namespace hlbm

@@ -30,19 +30,19 @@ __global__ void __launch_bounds__(32 * BY, 2) step3d_kernel(const __grid_constan
 
   float g[L::Q];
   gather<L, C>(fin, a.N, nx, ny, nz, x, y, z, g);
-  float dr, J[3], Pi;
-  moments<L>(g, dr, J, Pi);
+  float dr, acc, J[3], Pih;
+  moments_h<L>(g, dr, acc, J, Pih);
   const float rho = a.rho0 + dr;
-  float acc[3];
-  accel<3>(a, node, y, acc);
-  const float F0 = rho * acc[0], F1 = rho * acc[1], F2 = rho * acc[2];
+  float gacc[3];
+  accel<3>(a, node, y, gacc);
+  const float F0 = rho * gacc[0], F1 = rho * gacc[1], F2 = rho * gacc[2];
   const float inv_rho = 1.f / rho;
   const float ux = fmaf(0.5f, F0, J[0]) * inv_rho;
   const float uy = fmaf(0.5f, F1, J[1]) * inv_rho;
   const float uz = fmaf(0.5f, F2, J[2]) * inv_rho;
   const float uu = ux * ux + uy * uy + uz * uz;
   const float G2 = 2.f * (ux * F0 + uy * F1 + uz * F2);
-  const float tb_m = (Pi - dr * Dc - rho * uu + 0.5f * G2) * inv_rho * (1.f / Dc);
+  const float tb_m = (Pih - rho * uu + 0.5f * G2) * inv_rho * (1.f / Dc);
 
   if constexpr (MOM) {
     if (active) {
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(32 * BY, 2) step3d_kernel(const __grid_constan
         v[1] = (double)rho * ux;
         v[2] = (double)rho * uy;
         v[3] = (double)rho * uz;
-        v[4] = 0.5 * ((double)Pi + 0.5 * (double)G2);
+        v[4] = 0.5 * ((double)Pih + (double)Dc * dr + 0.5 * (double)G2);
         v[5] = bad ? 1.0 : 0.0;
       }
 #pragma unroll
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(32 * BY, 2) step3d_kernel(const __grid_constan
     }
   } else {
     NodeSrc s;
-    s.dr = dr;
+    s.dr = 0.f;  // density deviation re-enters in apply_poly_h
     s.rho = rho;
     s.tb = a.isothermal ? 0.f : tb_m;
     s.u[0] = ux * inv_c0;
@@ -94,7 +94,9 @@ __global__ void __launch_bounds__(32 * BY, 2) step3d_kernel(const __grid_constan
     s.sigma = 0.f;
     float K[20];
     poly3<L>(s, a.omega, a.beta, K);
-    apply_poly<L, 20>(g, K, 1.f - a.omega);
+    const float om1 = 1.f - a.omega;
+    K[0] = fmaf(-om1, acc, K[0]);
+    apply_poly_h<L, 20>(g, K, om1, dr);
     if (active) {
       T* __restrict__ fout = static_cast<T*>(a.fout);
       static_for<L::Q>([&](auto I) {

@@ -57,6 +57,44 @@ template <> struct Codec<ST_BF16> {
   __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+// exact for values that came from to_float of the same type
+template <class T> __device__ __forceinline__ T from_float(float v);
+template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// ------------------------------------------------------- lane arithmetic
+// The node arithmetic is written once for V = float (one node per thread)
+// and V = float2 (two nodes per thread, mapped onto Blackwell's paired FP32
+// instructions FADD2 / FMUL2 / FFMA2, which halve the issue slots of the
+// collision).  Every operation below rounds exactly like its scalar form.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <class V> __device__ __forceinline__ V splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
+template <class V> struct Lanes;
+template <> struct Lanes<float> { static constexpr int n = 1; };
+template <> struct Lanes<float2> { static constexpr int n = 2; };
+__device__ __forceinline__ float lane(float v, int) { return v; }
+__device__ __forceinline__ float lane(float2 v, int k) { return k ? v.y : v.x; }
+__device__ __forceinline__ void set_lane(float& v, int, float x) { v = x; }
+__device__ __forceinline__ void set_lane(float2& v, int k, float x) {
+  if (k) v.y = x;
+  else v.x = x;
+}
+template <class F> __device__ __forceinline__ float vmap(float a, F f) { return f(a); }
+template <class F> __device__ __forceinline__ float2 vmap(float2 a, F f) { return make_float2(f(a.x), f(a.y)); }
+
 // ----------------------------------------------------- compile-time helpers
 __host__ __device__ constexpr int ipow_i(int x, int n) { return n == 0 ? 1 : x * ipow_i(x, n - 1); }
 __host__ __device__ constexpr double ipow_d(double x, int n) { return n == 0 ? 1.0 : x * ipow_d(x, n - 1); }
@@ -127,33 +165,49 @@ __device__ __forceinline__ void gather(const typename C::T* __restrict__ f, long
 }
 
 // ----------------------------------------------------------------- moments
-// dr = sum w g (= rho - rho0), J = sum w c g (= sum c f^), Pi = sum w |c|^2 g
-// (= sum |c|^2 f^ - rho0 D c0^2); opposite pairs share the sum and difference.
-template <class L>
-__device__ __forceinline__ void moments(const float (&g)[L::Q], float& dr, float (&J)[3], float& Pi) {
-  dr = (float)L::w(0) * g[0];
-  J[0] = J[1] = J[2] = 0.f;
-  Pi = 0.f;
+// Moments of Eq. 4.5 in local-deviation form.  All g_i of a node are close to
+// its density deviation dr = rho - rho0, which can be O(1) (liquid-gas), while
+// velocity and temperature live in the differences.  So the sums run over
+// differences of nearly equal numbers (exact in floating point):
+//   d_i = g_i - g_0 (written back into g, d_0 = 0), acc = sum_{i>=1} w_i d_i,
+//   dr = g_0 + acc,  J = sum_i w_i c_i d_i (= sum_i c_i f^_i),
+//   Pih = sum_i w_i |c_i|^2 (g_i - dr) = sum_{i>=1} w_i |c_i|^2 d_i - D c0^2 acc
+//       (= sum_i |c_i|^2 f^_i - rho D c0^2).
+// Opposite pairs share the sum and difference of their d.
+template <class L, class V>
+__device__ __forceinline__ void moments_h(V (&g)[L::Q], V& dr, V& acc, V (&J)[3], V& Pih) {
+  const V g0 = g[0];
+  V a = splat<V>(0.f), p = splat<V>(0.f);
+  J[0] = J[1] = J[2] = splat<V>(0.f);
   static_for<L::NPAIR>([&](auto P) {
     constexpr int i = 2 * P + 1, j = 2 * P + 2;
-    const float s = g[i] + g[j], d = g[i] - g[j];
-    dr = fmaf((float)L::w(i), s, dr);
-    Pi = fmaf((float)(L::w(i) * L::norm2(i)), s, Pi);
+    const V di = vsub(g[i], g0), dj = vsub(g[j], g0);
+    g[i] = di;
+    g[j] = dj;
+    const V s = vadd(di, dj), d = vsub(di, dj);
+    a = vfma(splat<V>((float)L::w(i)), s, a);
+    p = vfma(splat<V>((float)(L::w(i) * L::norm2(i))), s, p);
     static_for<L::D>([&](auto A) {
-      constexpr int a = A;
-      if constexpr (L::c(i, a) != 0) J[a] = fmaf((float)(L::w(i) * L::c(i, a)), d, J[a]);
+      constexpr int ax = A;
+      if constexpr (L::c(i, ax) != 0) J[ax] = vfma(splat<V>((float)(L::w(i) * L::c(i, ax))), d, J[ax]);
     });
   });
+  g[0] = splat<V>(0.f);
+  acc = a;
+  dr = vadd(g0, a);
+  Pih = vfma(splat<V>(-(float)(L::D * L::cs2)), a, p);
 }
 
-template <class L>
-__device__ __forceinline__ float sum_w(const float (&g)[L::Q]) {
-  float dr = (float)L::w(0) * g[0];
+// dr alone, same summation (g is not modified).
+template <class L, class V>
+__device__ __forceinline__ V density_h(const V (&g)[L::Q]) {
+  const V g0 = g[0];
+  V a = splat<V>(0.f);
   static_for<L::NPAIR>([&](auto P) {
     constexpr int i = 2 * P + 1, j = 2 * P + 2;
-    dr = fmaf((float)L::w(i), g[i] + g[j], dr);
+    a = vfma(splat<V>((float)L::w(i)), vadd(vsub(g[i], g0), vsub(g[j], g0)), a);
   });
-  return dr;
+  return vadd(g0, a);
 }
 
 // ---------------------------------------------------------- pseudopotential
@@ -191,46 +245,51 @@ __device__ __forceinline__ void accel(const StepArgs& a, int node, int y, float 
 // ------------------------------------------------------ collision polynomial
 // Per-node inputs in xi units: u, F divided by c0; hG = rho theta (1 - 1/Pr)
 // c0 grad theta; sigma the trace coefficient of P_i.
-struct NodeSrc {
-  float dr, rho, tb;
-  float u[3], F[3], hG[3];
-  float sigma;
+template <class V>
+struct NodeSrcT {
+  V dr, rho, tb;
+  V u[3], F[3], hG[3];
+  V sigma;
 };
+using NodeSrc = NodeSrcT<float>;
 
 // Hermite moments of a unit-variance-plus-tb Gaussian, m_0..m_4.
-__device__ __forceinline__ void gauss_moments(float u, float tb, float (&m)[5]) {
-  const float u2 = u * u;
-  m[0] = 1.f;
+template <class V>
+__device__ __forceinline__ void gauss_moments(V u, V tb, V (&m)[5]) {
+  const V u2 = vmul(u, u);
+  m[0] = splat<V>(1.f);
   m[1] = u;
-  m[2] = u2 + tb;
-  m[3] = u * (u2 + 3.f * tb);
-  m[4] = u2 * (u2 + 6.f * tb) + 3.f * tb * tb;
+  m[2] = vadd(u2, tb);
+  m[3] = vmul(u, vfma(splat<V>(3.f), tb, u2));
+  m[4] = vfma(u2, vfma(splat<V>(6.f), tb, u2), vmul(splat<V>(3.f), vmul(tb, tb)));
 }
 
 // K[m] (monomial m of mono2) for D2Q37: 4th-order equilibrium + sources.
-template <class L>
-__device__ __forceinline__ void poly2(const NodeSrc& s, float omega, float beta, float (&K)[15]) {
-  float mx[5], my[5];
+template <class L, class V>
+__device__ __forceinline__ void poly2(const NodeSrcT<V>& s, float omega, float beta, V (&K)[15]) {
+  V mx[5], my[5];
   gauss_moments(s.u[0], s.tb, mx);
   gauss_moments(s.u[1], s.tb, my);
 #pragma unroll
-  for (int m = 0; m < 15; ++m) K[m] = 0.f;
+  for (int m = 0; m < 15; ++m) K[m] = splat<V>(0.f);
   static_for<5>([&](auto A) {
     static_for<5>([&](auto Bq) {
       constexpr int a = A, b = Bq;
       if constexpr (a + b <= L::FEQ_ORDER) {
-        float eq = (a == 0 && b == 0) ? s.dr : s.rho * mx[a] * my[b];
-        float src = 0.f;
+        const V eq = (a == 0 && b == 0) ? s.dr : vmul(s.rho, vmul(mx[a], my[b]));
+        V src = splat<V>(0.f);
         if constexpr (a + b >= 1 && a + b <= 3) {
-          if constexpr (a > 0) src = fmaf(s.F[0] * (float)a, mx[a > 0 ? a - 1 : 0] * my[b], src);
-          if constexpr (b > 0) src = fmaf(s.F[1] * (float)b, mx[a] * my[b > 0 ? b - 1 : 0], src);
+          if constexpr (a > 0)
+            src = vfma(vmul(s.F[0], splat<V>((float)a)), vmul(mx[a > 0 ? a - 1 : 0], my[b]), src);
+          if constexpr (b > 0)
+            src = vfma(vmul(s.F[1], splat<V>((float)b)), vmul(mx[a], my[b > 0 ? b - 1 : 0]), src);
         }
-        if constexpr ((a == 2 && b == 0) || (a == 0 && b == 2)) src += s.sigma;
-        if constexpr (a == 3 && b == 0) src = fmaf(3.f, s.hG[0], src);
-        if constexpr (a == 2 && b == 1) src += s.hG[1];
-        if constexpr (a == 1 && b == 2) src += s.hG[0];
-        if constexpr (a == 0 && b == 3) src = fmaf(3.f, s.hG[1], src);
-        const float Bab = fmaf(omega, eq, beta * src);
+        if constexpr ((a == 2 && b == 0) || (a == 0 && b == 2)) src = vadd(src, s.sigma);
+        if constexpr (a == 3 && b == 0) src = vfma(splat<V>(3.f), s.hG[0], src);
+        if constexpr (a == 2 && b == 1) src = vadd(src, s.hG[1]);
+        if constexpr (a == 1 && b == 2) src = vadd(src, s.hG[0]);
+        if constexpr (a == 0 && b == 3) src = vfma(splat<V>(3.f), s.hG[1], src);
+        const V Bab = vfma(splat<V>(omega), eq, vmul(splat<V>(beta), src));
         // He_a(cx / c0) He_b(cy / c0) / (a! b!) -> monomials c_x^p c_y^q
         static_for<5>([&](auto Pp) {
           static_for<5>([&](auto Qq) {
@@ -239,7 +298,7 @@ __device__ __forceinline__ void poly2(const NodeSrc& s, float omega, float beta,
               constexpr float cf = (float)((double)(he(a, p) * he(b, q)) /
                                            (fact_d(a) * fact_d(b) * ipow_d(L::c0, p + q)));
               constexpr int m = mono2_index(p, q);
-              K[m] = fmaf(cf, Bab, K[m]);
+              K[m] = vfma(splat<V>(cf), Bab, K[m]);
             }
           });
         });
@@ -249,42 +308,45 @@ __device__ __forceinline__ void poly2(const NodeSrc& s, float omega, float beta,
 }
 
 // K[m] (monomial m of mono3) for D3Q39: 3rd-order equilibrium + body force.
-template <class L>
-__device__ __forceinline__ void poly3(const NodeSrc& s, float omega, float beta, float (&K)[20]) {
-  float mx[5], my[5], mz[5];
+template <class L, class V>
+__device__ __forceinline__ void poly3(const NodeSrcT<V>& s, float omega, float beta, V (&K)[20]) {
+  V mx[5], my[5], mz[5];
   gauss_moments(s.u[0], s.tb, mx);
   gauss_moments(s.u[1], s.tb, my);
   gauss_moments(s.u[2], s.tb, mz);
 #pragma unroll
-  for (int m = 0; m < 20; ++m) K[m] = 0.f;
+  for (int m = 0; m < 20; ++m) K[m] = splat<V>(0.f);
   static_for<4>([&](auto A) {
     static_for<4>([&](auto Bq) {
       static_for<4>([&](auto Cr) {
         constexpr int a = A, b = Bq, c = Cr;
         if constexpr (a + b + c <= L::FEQ_ORDER) {
-          float eq = (a == 0 && b == 0 && c == 0) ? s.dr : s.rho * mx[a] * my[b] * mz[c];
-          float src = 0.f;
+          const V eq = (a == 0 && b == 0 && c == 0) ? s.dr : vmul(s.rho, vmul(mx[a], vmul(my[b], mz[c])));
+          V src = splat<V>(0.f);
           if constexpr (a + b + c >= 1) {
-            if constexpr (a > 0) src = fmaf(s.F[0] * (float)a, mx[a > 0 ? a - 1 : 0] * my[b] * mz[c], src);
-            if constexpr (b > 0) src = fmaf(s.F[1] * (float)b, mx[a] * my[b > 0 ? b - 1 : 0] * mz[c], src);
-            if constexpr (c > 0) src = fmaf(s.F[2] * (float)c, mx[a] * my[b] * mz[c > 0 ? c - 1 : 0], src);
+            if constexpr (a > 0)
+              src = vfma(vmul(s.F[0], splat<V>((float)a)), vmul(mx[a > 0 ? a - 1 : 0], vmul(my[b], mz[c])), src);
+            if constexpr (b > 0)
+              src = vfma(vmul(s.F[1], splat<V>((float)b)), vmul(mx[a], vmul(my[b > 0 ? b - 1 : 0], mz[c])), src);
+            if constexpr (c > 0)
+              src = vfma(vmul(s.F[2], splat<V>((float)c)), vmul(mx[a], vmul(my[b], mz[c > 0 ? c - 1 : 0])), src);
           }
           if constexpr ((a == 2 && b == 0 && c == 0) || (a == 0 && b == 2 && c == 0) ||
                         (a == 0 && b == 0 && c == 2))
-            src += s.sigma;
+            src = vadd(src, s.sigma);
           // [delta hG] components: (3,0,0) -> 3 hGx, (2,1,0) -> hGy, (1,2,0) -> hGx, ...
           if constexpr (a + b + c == 3) {
-            if constexpr (a == 3) src = fmaf(3.f, s.hG[0], src);
-            if constexpr (b == 3) src = fmaf(3.f, s.hG[1], src);
-            if constexpr (c == 3) src = fmaf(3.f, s.hG[2], src);
-            if constexpr (a == 2 && b == 1) src += s.hG[1];
-            if constexpr (a == 2 && c == 1) src += s.hG[2];
-            if constexpr (b == 2 && a == 1) src += s.hG[0];
-            if constexpr (b == 2 && c == 1) src += s.hG[2];
-            if constexpr (c == 2 && a == 1) src += s.hG[0];
-            if constexpr (c == 2 && b == 1) src += s.hG[1];
+            if constexpr (a == 3) src = vfma(splat<V>(3.f), s.hG[0], src);
+            if constexpr (b == 3) src = vfma(splat<V>(3.f), s.hG[1], src);
+            if constexpr (c == 3) src = vfma(splat<V>(3.f), s.hG[2], src);
+            if constexpr (a == 2 && b == 1) src = vadd(src, s.hG[1]);
+            if constexpr (a == 2 && c == 1) src = vadd(src, s.hG[2]);
+            if constexpr (b == 2 && a == 1) src = vadd(src, s.hG[0]);
+            if constexpr (b == 2 && c == 1) src = vadd(src, s.hG[2]);
+            if constexpr (c == 2 && a == 1) src = vadd(src, s.hG[0]);
+            if constexpr (c == 2 && b == 1) src = vadd(src, s.hG[1]);
           }
-          const float Babc = fmaf(omega, eq, beta * src);
+          const V Babc = vfma(splat<V>(omega), eq, vmul(splat<V>(beta), src));
           static_for<4>([&](auto Pp) {
             static_for<4>([&](auto Qq) {
               static_for<4>([&](auto Rr) {
@@ -293,7 +355,7 @@ __device__ __forceinline__ void poly3(const NodeSrc& s, float omega, float beta,
                   constexpr float cf = (float)((double)(he(a, p) * he(b, q) * he(c, r)) /
                                                (fact_d(a) * fact_d(b) * fact_d(c) * ipow_d(L::c0, p + q + r)));
                   constexpr int m = mono3_index(p, q, r);
-                  K[m] = fmaf(cf, Babc, K[m]);
+                  K[m] = vfma(splat<V>(cf), Babc, K[m]);
                 }
               });
             });
@@ -334,6 +396,52 @@ __device__ __forceinline__ void apply_poly(float (&g)[L::Q], const float (&K)[NM
     });
     g[i] = fmaf(om1, g[i], E + O);
     g[j] = fmaf(om1, g[j], E - O);
+  });
+}
+
+
+// Collision in local-deviation form.  With d_i = g_i - g_0 and dr, acc from
+// moments_h, and K computed with B_00 = 0 and K_00 reduced by (1 - omega) acc,
+//   g*_i = dr + [(1 - omega) d_i + P(c_i)]
+// equals (1 - omega) g_i + P_full(c_i) (P_full with B_00 = omega dr), but only
+// small numbers pass through the arithmetic before the final add of dr.
+template <class L, int NM, class V>
+__device__ __forceinline__ void apply_poly_h(V (&g)[L::Q], const V (&K)[NM], float om1, V dr) {
+  const V o1 = splat<V>(om1);
+  g[0] = vadd(dr, K[0]);
+  static_for<L::NPAIR>([&](auto P) {
+    constexpr int i = 2 * P + 1, j = 2 * P + 2;
+    constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    V E = K[0], O = splat<V>(0.f);
+    bool have_o = false;
+    static_for<NM>([&](auto M) {
+      constexpr int m = M;
+      if constexpr (m > 0) {
+        constexpr int px = (NM == 15) ? mono2(m, 0) : mono3(m, 0);
+        constexpr int py = (NM == 15) ? mono2(m, 1) : mono3(m, 1);
+        constexpr int pz = (NM == 15) ? 0 : mono3(m, 2);
+        constexpr int mv = ipow_i(cx, px) * ipow_i(cy, py) * ipow_i(cz, pz);
+        if constexpr (mv != 0) {
+          if constexpr ((px + py + pz) % 2 == 0) {
+            if constexpr (mv == 1) E = vadd(E, K[m]);
+            else E = vfma(splat<V>((float)mv), K[m], E);
+          } else {
+            if (!have_o) {
+              O = (mv == 1) ? K[m] : vmul(splat<V>((float)mv), K[m]);
+              have_o = true;
+            } else if constexpr (mv == 1) {
+              O = vadd(O, K[m]);
+            } else if constexpr (mv == -1) {
+              O = vsub(O, K[m]);
+            } else {
+              O = vfma(splat<V>((float)mv), K[m], O);
+            }
+          }
+        }
+      }
+    });
+    g[i] = vadd(dr, vfma(o1, g[i], vadd(E, O)));
+    g[j] = vadd(dr, vfma(o1, g[j], vsub(E, O)));
   });
 }
 

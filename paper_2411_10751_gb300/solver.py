@@ -148,8 +148,8 @@ class HLBM:
     def step_count(self) -> int:
         return int(abi.hlbm_step_count(self.ctx))
 
-    def set_tile(self, rows: int) -> None:
-        self._chk(abi.hlbm_set_tile(self.ctx, int(rows)))
+    def set_tile(self, rows: int, nodes_per_thread: int = 0) -> None:
+        self._chk(abi.hlbm_set_tile(self.ctx, int(rows), int(nodes_per_thread)))
 
     def synchronize(self) -> None:
         self._chk(abi.hlbm_synchronize(self.ctx))
