@@ -167,6 +167,31 @@ hlbm_status hlbm_destroy(hlbm_ctx* ctx);
  * w[Q], *cs2 = c0^2, returns Q (0 on bad lattice).  Any pointer may be NULL. */
 int hlbm_lattice_info(int lattice, int* c, double* w, double* cs2);
 
+/* Domain totals of a population buffer without allocating any device memory.
+ * The paper has no counterpart: this serves callers that must not allocate
+ * device memory while they run (device memory handed out up front by another
+ * framework under a fixed budget, or an environment that forbids allocation
+ * after start-up); hlbm_diag needs the context's workspace for its scratch.
+ *   populations  device pointer to Q * nodes stored values laid out as a
+ *                context's state ([Q][nz][ny][nx], storage type `storage`,
+ *                g_i = (f_i - w_i rho0) / w_i), e.g. the first population
+ *                buffer of memory bound with hlbm_bind_memory after an even
+ *                number of steps
+ *   out          host array of D + 2 doubles: sum f (mass), sum c f
+ *                (momentum), sum |c|^2 f / 2 (energy) over all nodes and
+ *                velocities.  Streaming does not change these totals; without
+ *                a body force they equal hlbm_diag's mass, momentum and energy
+ *   cuda_stream  stream to run on (0: legacy default stream); the call
+ *                synchronises it
+ * Scratch is a 1 MiB static device array inside the library, held by every
+ * GPU that loads it until the process exits; it limits a call to 1 ..
+ * 33,554,432 nodes (HLBM_EINVAL beyond, with a message on stderr).  All calls
+ * share it and overwrite what they use: calls that overlap on the GPU race.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture. */
+hlbm_status hlbm_population_sums_noalloc(int lattice, long long nodes, int storage, double rho0,
+                                         const void* populations, void* cuda_stream, double* out);
+
 #ifdef __cplusplus
 }
 #endif
