@@ -148,11 +148,22 @@ def _max_over_ranks(ws, x: float) -> float:
     return float(t.item())
 
 
-def time_device(case, storage, steps, warmup, ws, lrank):
+def tuned_schedule(case, storage, lrank):
+    """Autotuned (rows, nodes per thread, persistent) for this workload (untimed)."""
+    import torch
+    from paper_2411_10751_gb300 import autotune
+    with torch.cuda.device(lrank):
+        return autotune.tune(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params,
+                             case.rho, case.u, case.theta, storage=storage)
+
+
+def time_device(case, storage, steps, warmup, ws, lrank, schedule=None):
     """Device-resident run: K steps timed with CUDA events on the context's stream."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM
     g = HLBM(case.lattice, case.nx, case.ny, 1, case.tau_hat, case.params, storage=storage, device=lrank)
+    if schedule:
+        g.set_tile(*schedule)
     g.init(case.rho, case.u, case.theta)
     g.step(warmup)
     g.synchronize()
@@ -174,12 +185,14 @@ def time_device(case, storage, steps, warmup, ws, lrank):
     return ms, clk.summary(), d
 
 
-def time_e2e(case, storage, steps, ws, lrank):
+def time_e2e(case, storage, steps, ws, lrank, schedule=None):
     """Through the public API with host buffers: pinned host fields -> hlbm_init
     (H2D), K steps, hlbm_moments to pinned host buffers (D2H); wall time."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM
     g = HLBM(case.lattice, case.nx, case.ny, 1, case.tau_hat, case.params, storage=storage, device=lrank)
+    if schedule:
+        g.set_tile(*schedule)
     pin = {k: torch.from_numpy(np.asarray(getattr(case, k), np.float32)).pin_memory() for k in ("rho", "u", "theta")}
     out = {k: torch.empty_like(pin[k]).pin_memory() for k in pin}
     g.init(pin["rho"].numpy(), pin["u"].numpy(), pin["theta"].numpy())   # warm-up of the path
@@ -293,7 +306,8 @@ def main():
     pkg.load()
 
     case = W.thermal_decay(n=1024)
-    ms, clocks, diag = time_device(case, args.storage, args.steps, args.warmup, ws, lrank)
+    sched = tuned_schedule(case, args.storage, lrank)
+    ms, clocks, diag = time_device(case, args.storage, args.steps, args.warmup, ws, lrank, sched)
     ms = _max_over_ranks(ws, ms)
     nodes = case.nodes
     value = nodes * args.steps * ws / (ms * 1e-3) / 1e6
@@ -304,7 +318,7 @@ def main():
     peak, peak_kind = _peaks()
     khash = _kernel_source_hash()
 
-    e2e_ms, h2d, d2h = time_e2e(case, args.storage, args.steps, ws, lrank)
+    e2e_ms, h2d, d2h = time_e2e(case, args.storage, args.steps, ws, lrank, sched)
     e2e_ms = _max_over_ranks(ws, e2e_ms)
 
     variants = None
@@ -317,9 +331,10 @@ def main():
                 if st == args.storage:
                     continue
                 k = min(args.steps, 4000)
-                vms, _, _ = time_device(case, st, k, args.warmup, 1, lrank)
+                vsched = tuned_schedule(case, st, lrank)
+                vms, _, _ = time_device(case, st, k, args.warmup, 1, lrank, vsched)
                 e = 4 if st == "f32" else 2
-                variants[st] = {"MLUPS": nodes * k / (vms * 1e-3) / 1e6,
+                variants[st] = {"MLUPS": nodes * k / (vms * 1e-3) / 1e6, "schedule": list(vsched),
                                 "achieved_GBs": 2 * 37 * e * nodes / (vms * 1e-3 / k) / 1e9,
                                 "frac_of_" + peak_kind: 2 * 37 * e * nodes / (vms * 1e-3 / k) / 1e9 / peak}
             errors = storage_errors()
@@ -333,6 +348,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes_per_gpu": nodes, "storage": args.storage,
+                       "schedule": {"rows": sched[0], "nodes_per_thread": sched[1],
+                                    "persistent": sched[2] == 2, "chosen_by": "autotune"},
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (2 x %d MB population buffers), no flush" %
                              (37 * elem * nodes // 2 ** 20)},

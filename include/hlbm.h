@@ -143,10 +143,11 @@ hlbm_status hlbm_load(hlbm_ctx* ctx, const void* host_buf, size_t bytes);
 long long hlbm_step_count(const hlbm_ctx* ctx);
 
 /* Schedule of the fused step: tile rows per CTA (2D: 4, 8 or 16; D3Q39: 4
- * or 8; 0 = default 8) and nodes per thread (1, or 2 on paired FP32 lanes
- * with 8 or 16 rows; 0 = default 2; D2Q37 only).  Chosen by the autotuner;
- * results agree to rounding across schedules. */
-hlbm_status hlbm_set_tile(hlbm_ctx* ctx, int rows, int nodes_per_thread);
+ * or 8; 0 = default 8), nodes per thread (1, or 2 on paired FP32 lanes
+ * with 8 or 16 rows; 0 = default 2; D2Q37 only) and persistent CTAs that
+ * prefetch their next tile (0 = default off, 1 = off, 2 = on; D2Q37 only).
+ * Chosen by the autotuner; results agree to rounding across schedules. */
+hlbm_status hlbm_set_tile(hlbm_ctx* ctx, int rows, int nodes_per_thread, int persistent);
 
 /* Waits for all work on the context's stream.  Returns HLBM_ETIMEOUT (and
  * enters the error state) if a kernel reported an expired bounded wait. */

@@ -63,7 +63,7 @@ _sigs = {
     "hlbm_save": ([_vp, _vp, _sz], _i),
     "hlbm_load": ([_vp, _vp, _sz], _i),
     "hlbm_step_count": ([_vp], _ll),
-    "hlbm_set_tile": ([_vp, _i, _i], _i),
+    "hlbm_set_tile": ([_vp, _i, _i, _i], _i),
     "hlbm_synchronize": ([_vp], _i),
     "hlbm_set_wait_timeout": ([_vp, _d], _i),
     "hlbm_last_error": ([_vp], C.c_char_p),

@@ -27,6 +27,7 @@ struct hlbm_ctx {
   size_t elem = 4;
   int rows = 8;
   int npt = 2;
+  int persistent = 0;
 
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -208,6 +209,7 @@ StepArgs make_args(const hlbm_ctx* c) {
   a.eos_T = (float)c->p.eos_T;
   a.status = c->status;
   a.tma = c->tma_ok ? 1 : 0;
+  a.persistent = c->persistent;
   a.wait_ns = c->wait_ns;
   a.debug_skip_tma = c->debug_skip_tma;
   const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
@@ -582,8 +584,9 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
 
 long long hlbm_step_count(const hlbm_ctx* c) { return c ? c->steps : -1; }
 
-hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread) {
+hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread, int persistent) {
   if (!c) return HLBM_EINVAL;
+  if (persistent < 0 || persistent > 2) return fail(c, HLBM_EINVAL, "persistent must be 0 (default off), 1 (off) or 2 (on)");
   if (rows == 0) rows = 8;
   if (nodes_per_thread == 0) nodes_per_thread = 2;
   if (rows != 4 && rows != 8 && rows != 16) return fail(c, HLBM_EINVAL, "rows must be 4, 8 or 16");
@@ -592,6 +595,7 @@ hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread) {
   if (c->lattice == 1 && rows == 16) return fail(c, HLBM_EINVAL, "D3Q39 tiles have 4 or 8 rows");
   c->rows = rows;
   c->npt = nodes_per_thread;
+  c->persistent = (persistent == 2) ? 1 : 0;
   drop_graphs(c);
   return HLBM_OK;
 }

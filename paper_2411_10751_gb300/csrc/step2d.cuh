@@ -24,6 +24,7 @@
 #include "step_common.cuh"
 #include "tma.cuh"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace hlbm {
@@ -112,12 +113,57 @@ constexpr int min_ctas2() {
   return by_smem < 1 ? 1 : (by_smem < cap ? by_smem : cap);
 }
 
-// NPT nodes per thread: thread (tx, ty) owns tile rows ty + k * BY / NPT,
-// k < NPT; with NPT = 2 the node arithmetic runs on float2 lanes.
-template <int ST, int KIND, bool MOM, int BY, int NPT>
-__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, NPT>()))
-    step2d_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap,
-                  const __grid_constant__ CUtensorMap tmap_out) {
+// Issues the Q staging boxes of the tile at (x0, y0) against `bar`.
+template <class Cf>
+__device__ __forceinline__ void issue_tile(typename Cf::T* sp, const CUtensorMap* tmap, uint64_t* bar, int x0, int y0,
+                                           int skip) {
+  using L = D2Q37;
+  constexpr int H = Cf::H;
+  mbar_arrive_expect_tx(bar, Cf::TX_BYTES);
+  if (!skip) {
+    static_for<37>([&](auto I) {
+      constexpr int i = I;
+      tma_load_3d(sp + i * Cf::PLANE, tmap, x0 - H - L::c(i, 0) - Cf::rem(i), y0 - H - L::c(i, 1), i, bar);
+    });
+  }
+}
+
+// Whether the tile's boxes lie inside the domain (no periodic wrap needed).
+template <class Cf>
+__device__ __forceinline__ bool tile_boxed(const StepArgs& a, int x0, int y0) {
+  constexpr int H = Cf::H;
+  return a.tma && (x0 - H - 3 - (Cf::A - 1) >= 0) && (x0 - H + 3 + Cf::WB <= a.nx) && (y0 - H - 3 >= 0) &&
+         (y0 - H + 3 + Cf::HB <= a.ny);
+}
+
+// Edge tile: every region node gathers its Q pulled populations with periodic
+// wrap (independent loads) and writes them into the staged layout.
+template <class Cf, int NT>
+__device__ __forceinline__ void fill_tile_wrapped(const StepArgs& a, typename Cf::T* sp, int x0, int y0, int tid) {
+  using L = D2Q37;
+  using T = typename Cf::T;
+  constexpr int H = Cf::H;
+  const T* __restrict__ fin = static_cast<const T*>(a.fin);
+  for (int k = tid; k < Cf::RW * Cf::RH; k += NT) {
+    const int ry = k / Cf::RW, rx = k - ry * Cf::RW;
+    const int X = wrapm(x0 - H + rx, a.nx), Y = wrapm(y0 - H + ry, a.ny);
+    float gk[37];
+    gather<L, typename Cf::C>(fin, a.N, a.nx, a.ny, 1, X, Y, 0, gk);
+    const int base = ry * Cf::WB + rx;
+    static_for<37>([&](auto I) {
+      constexpr int i = I;
+      sp[i * Cf::PLANE + base + Cf::rem(i)] = from_float<T>(gk[i]);
+    });
+  }
+}
+
+// The work on one staged tile: moments, neighbour fields, sources, collision
+// and stores.  `staged_done()` runs once every read of the staging buffer has
+// finished (after a CTA barrier), so a caller may start refilling it then.
+// TMA_STORE: results leave through the staging buffer by bulk tensor stores.
+template <int ST, int KIND, bool MOM, int BY, int NPT, bool TMA_STORE, class Done>
+__device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMap* tmap_out, unsigned char* smem,
+                                             int x0, int y0, Done&& staged_done) {
   using Cf = Cfg2<ST, KIND, MOM, BY>;
   using L = D2Q37;
   using T = typename Cf::T;
@@ -128,61 +174,11 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
   using Fr = Frame2<BX, BY, (H > 0 ? H : 1)>;
   constexpr float Dc = (float)(2.0 * L::cs2);
   constexpr float inv_c0 = (float)(1.0 / L::c0);
-
-  extern __shared__ __align__(128) unsigned char smem[];
   T* sp = reinterpret_cast<T*>(smem);
   float* aux = reinterpret_cast<float*>(smem + Cf::POP_BYTES);
   double* red = reinterpret_cast<double*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
-
   const int nx = a.nx, ny = a.ny;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-
-  // ---- stage the region's pulled populations
-  const bool boxed = a.tma && (x0 - H - 3 - (Cf::A - 1) >= 0) && (x0 - H + 3 + Cf::WB <= nx) &&
-                     (y0 - H - 3 >= 0) && (y0 - H + 3 + Cf::HB <= ny) && ((smem_u32(smem) & 127u) == 0);
-  if (boxed) {
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-      mbar_arrive_expect_tx(bar, Cf::TX_BYTES);
-      if (!a.debug_skip_tma) {
-        static_for<37>([&](auto I) {
-          constexpr int i = I;
-          tma_load_3d(sp + i * Cf::PLANE, &tmap, x0 - H - L::c(i, 0) - Cf::rem(i), y0 - H - L::c(i, 1), i, bar);
-        });
-      }
-    }
-    bool ok = mbar_wait_bounded(bar, 0, a.wait_ns);
-    if (!__syncthreads_and(ok)) {
-      // copies did not complete: report, give in-flight copies a second bounded
-      // wait, and leave without touching the outputs
-      if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
-      mbar_wait_bounded(bar, 0, a.wait_ns);
-      __syncthreads();
-      return;
-    }
-  } else {
-    // edge tile: every region node gathers its Q pulled populations with
-    // periodic wrap (independent loads) and writes them into the staged layout
-    const T* __restrict__ fin = static_cast<const T*>(a.fin);
-    for (int k = tid; k < Cf::RW * Cf::RH; k += NT) {
-      const int ry = k / Cf::RW, rx = k - ry * Cf::RW;
-      const int X = wrapm(x0 - H + rx, nx), Y = wrapm(y0 - H + ry, ny);
-      float gk[37];
-      gather<L, typename Cf::C>(fin, a.N, nx, ny, 1, X, Y, 0, gk);
-      const int base = ry * Cf::WB + rx;
-      static_for<37>([&](auto I) {
-        constexpr int i = I;
-        sp[i * Cf::PLANE + base + Cf::rem(i)] = from_float<T>(gk[i]);
-      });
-    }
-    __syncthreads();
-  }
 
   // ---- this thread's nodes (lane k: tile row ty + k * TR)
   const int x = (x0 + tx < nx) ? x0 + tx : (x0 + tx) % nx;
@@ -232,6 +228,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
       aux[j * Fr::SW + i] = psi_of<L>(a, a.rho0 + density_h<L>(gh));
     }
     __syncthreads();
+    staged_done();
     // F^SC = -G psi(x) sum_i w_i psi(x + c_i) c_i with G = -1
     V sx = splat<V>(0.f), sy = splat<V>(0.f);
     static_for<L::NPAIR>([&](auto P) {
@@ -302,6 +299,10 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
   } else {
     NodeSrcT<V> s;
     s.hG[0] = s.hG[1] = s.hG[2] = splat<V>(0.f);
+    if constexpr (KIND == KIND_LOCAL) {
+      __syncthreads();
+      staged_done();
+    }
     if constexpr (KIND == KIND_THERMAL) {
       // theta - 1 on the tile and its 4-neighbour ring, then grad theta
 #pragma unroll
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
         aux[j * Fr::SW + i] = theta_bar_local<L>(a, gh, hy * nx + hx, hy);
       }
       __syncthreads();
+      staged_done();
       V gtx, gty;
 #pragma unroll
       for (int k = 0; k < NPT; ++k) {
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
     const float om1 = 1.f - a.omega;
     K[0] = vfma(splat<V>(-om1), acc, K[0]);
     apply_poly_h<L, 15>(g, K, om1, dr);
-    if (a.tma_store) {
+    if (TMA_STORE && a.tma_store) {
       // stage the tile's results densely in the (now unused) input planes and
       // write each plane with one bulk tensor store; out-of-domain rows and
       // columns of a ragged tile are clipped by the copy
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
       if (tid == 0) {
         static_for<37>([&](auto I) {
           constexpr int i = I;
-          tma_store_3d(&tmap_out, sp + i * Cf::PLANE, x0, y0, i);
+          tma_store_3d(tmap_out, sp + i * Cf::PLANE, x0, y0, i);
         });
         bulk_commit();
         bulk_wait_all();
@@ -379,6 +381,105 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
   }
 }
 
+// One CTA per tile.
+template <int ST, int KIND, bool MOM, int BY, int NPT>
+__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, NPT>()))
+    step2d_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap,
+                  const __grid_constant__ CUtensorMap tmap_out) {
+  using Cf = Cfg2<ST, KIND, MOM, BY>;
+  constexpr int NT = 32 * BY / NPT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  typename Cf::T* sp = reinterpret_cast<typename Cf::T*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * BY;
+  if (tile_boxed<Cf>(a, x0, y0) && ((smem_u32(smem) & 127u) == 0)) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) issue_tile<Cf>(sp, &tmap, bar, x0, y0, a.debug_skip_tma);
+    const bool ok = mbar_wait_bounded(bar, 0, a.wait_ns);
+    if (!__syncthreads_and(ok)) {
+      // copies did not complete: report, give in-flight copies a second bounded
+      // wait, and leave without touching the outputs
+      if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
+      mbar_wait_bounded(bar, 0, a.wait_ns);
+      __syncthreads();
+      return;
+    }
+  } else {
+    fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
+    __syncthreads();
+  }
+  process_tile<ST, KIND, MOM, BY, NPT, true>(a, &tmap_out, smem, x0, y0, [] {});
+}
+
+// Persistent CTAs: each walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// (row-major), and issues the next tile's boxes into the staging buffer as
+// soon as the current tile's last staged read is done, so the load overlaps
+// the current tile's collision and stores.
+template <int ST, int KIND, int BY, int NPT>
+__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY, NPT>()))
+    step2d_persistent_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap) {
+  using Cf = Cfg2<ST, KIND, false, BY>;
+  constexpr int NT = 32 * BY / NPT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  typename Cf::T* sp = reinterpret_cast<typename Cf::T*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int ntx = (a.nx + 31) / 32;
+  const int ntiles = ntx * ((a.ny + BY - 1) / BY);
+  const bool aligned = (smem_u32(smem) & 127u) == 0;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int t = blockIdx.x;
+  auto origin = [&](int tt, int& x0, int& y0) {
+    const int by = tt / ntx;
+    x0 = (tt - by * ntx) * 32;
+    y0 = by * BY;
+  };
+  if (t < ntiles && tid == 0) {
+    int x0, y0;
+    origin(t, x0, y0);
+    if (aligned && tile_boxed<Cf>(a, x0, y0)) issue_tile<Cf>(sp, &tmap, bar, x0, y0, a.debug_skip_tma);
+  }
+  for (; t < ntiles; t += gridDim.x) {
+    int x0, y0;
+    origin(t, x0, y0);
+    if (aligned && tile_boxed<Cf>(a, x0, y0)) {
+      const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
+        mbar_wait_bounded(bar, phase, a.wait_ns);
+        __syncthreads();
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
+      __syncthreads();
+    }
+    const int tn = t + gridDim.x;
+    process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, [&] {
+      if (tid == 0 && tn < ntiles) {
+        int xn, yn;
+        origin(tn, xn, yn);
+        if (aligned && tile_boxed<Cf>(a, xn, yn)) {
+          fence_proxy_async_smem();
+          issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma);
+        }
+      }
+    });
+    __syncthreads();  // the shared aux tile is reused by the next tile
+  }
+}
+
 // Box geometry of the launch configuration (for the host's tensor maps).
 template <int ST, int KIND, bool MOM, int BY>
 void box_of(int& wb, int& hb) {
@@ -392,13 +493,41 @@ int rows_of() {
 
 template <int ST, int KIND, bool MOM, int BY, int NPT = 1>
 cudaError_t configure2() {
-  return cudaFuncSetAttribute(step2d_kernel<ST, KIND, MOM, BY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Cfg2<ST, KIND, MOM, BY>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(step2d_kernel<ST, KIND, MOM, BY, NPT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<ST, KIND, MOM, BY>::SMEM);
+  if (e != cudaSuccess || MOM) return e;
+  return cudaFuncSetAttribute(step2d_persistent_kernel<ST, KIND, BY, NPT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<ST, KIND, false, BY>::SMEM);
+}
+
+// CTAs of a persistent launch: the resident CTAs per SM times the SM count.
+template <int ST, int KIND, int BY, int NPT>
+int persistent_ctas() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_persistent_kernel<ST, KIND, BY, NPT>, 32 * BY / NPT,
+                                                  Cfg2<ST, KIND, false, BY>::SMEM);
+    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return n;
 }
 
 template <int ST, int KIND, bool MOM, int BY, int NPT = 1>
 cudaError_t launch2(const StepArgs& a, const CUtensorMap* tmaps, cudaStream_t s) {
   using Cf = Cfg2<ST, KIND, MOM, BY>;
+  if constexpr (!MOM) {
+    if (a.persistent) {
+      const int tiles = ((a.nx + 31) / 32) * ((a.ny + BY - 1) / BY);
+      const int ctas = std::min(tiles, persistent_ctas<ST, KIND, BY, NPT>());
+      CUtensorMap tm{};
+      if (tmaps) tm = tmaps[0];
+      step2d_persistent_kernel<ST, KIND, BY, NPT><<<ctas, dim3(32, BY / NPT, 1), Cf::SMEM, s>>>(a, tm);
+      return cudaGetLastError();
+    }
+  }
   const dim3 grid((a.nx + 31) / 32, (a.ny + BY - 1) / BY, 1);
   const dim3 block(32, BY / NPT, 1);
   CUtensorMap tm{}, tmo{};

@@ -148,8 +148,9 @@ class HLBM:
     def step_count(self) -> int:
         return int(abi.hlbm_step_count(self.ctx))
 
-    def set_tile(self, rows: int, nodes_per_thread: int = 0) -> None:
-        self._chk(abi.hlbm_set_tile(self.ctx, int(rows), int(nodes_per_thread)))
+    def set_tile(self, rows: int, nodes_per_thread: int = 0, persistent: int = 0) -> None:
+        """Schedule: rows per tile, nodes per thread, persistent (0 default, 1 off, 2 on)."""
+        self._chk(abi.hlbm_set_tile(self.ctx, int(rows), int(nodes_per_thread), int(persistent)))
 
     def synchronize(self) -> None:
         self._chk(abi.hlbm_synchronize(self.ctx))

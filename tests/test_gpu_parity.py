@@ -36,10 +36,10 @@ def rel_err(m_gpu, m_ora):
     return er, eu, et
 
 
-def run_pair(HLBM, case, steps, storage="f32", rows=None, force_kind="field", npt=0):
+def run_pair(HLBM, case, steps, storage="f32", rows=None, force_kind="field", npt=0, persistent=0):
     g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage)
     if rows:
-        g.set_tile(rows, npt)
+        g.set_tile(rows, npt, persistent)
     o = Oracle(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params)
     if case.gfield is not None:
         o.set_force_field(case.gfield)
@@ -82,28 +82,29 @@ def test_thermal_parity_ragged(HLBM, nx, ny, steps):
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
-SCHEDULES = [(4, 1), (8, 1), (8, 2), (16, 1), (16, 2)]
+# (rows, nodes per thread, persistent: 1 off / 2 on)
+SCHEDULES = [(4, 1, 1), (8, 1, 1), (8, 2, 1), (16, 1, 1), (16, 2, 1), (4, 1, 2), (8, 1, 2), (8, 2, 2), (16, 2, 2)]
 
 
-@pytest.mark.parametrize("rows,npt", SCHEDULES)
-def test_thermal_schedules(HLBM, rows, npt):
+@pytest.mark.parametrize("rows,npt,pers", SCHEDULES)
+def test_thermal_schedules(HLBM, rows, npt, pers):
     # 200 x 120: interior tiles take the TMA path, edge tiles the gather path
     c = W.thermal_decay(nx=200, ny=120, tau_hat=0.7, Pr=0.71)
-    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt)
+    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt, persistent=pers)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
-@pytest.mark.parametrize("rows,npt", SCHEDULES)
-def test_droplet_schedules(HLBM, rows, npt):
+@pytest.mark.parametrize("rows,npt,pers", SCHEDULES)
+def test_droplet_schedules(HLBM, rows, npt, pers):
     c = W.droplet(nx=160, ny=96, r0=25.0, k=1.5672)
-    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt)
+    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt, persistent=pers)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
-@pytest.mark.parametrize("rows,npt", SCHEDULES)
-def test_kolmogorov_schedules(HLBM, rows, npt):
+@pytest.mark.parametrize("rows,npt,pers", SCHEDULES)
+def test_kolmogorov_schedules(HLBM, rows, npt, pers):
     c = W.kolmogorov(nx=160, ny=96)
-    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt, force_kind="profile")
+    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt, force_kind="profile", persistent=pers)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
