@@ -164,6 +164,24 @@ const char* hlbm_last_error(const hlbm_ctx* ctx);
 
 hlbm_status hlbm_destroy(hlbm_ctx* ctx);
 
+/* Gradient of the kinetic energy L = sum_x rho |u|^2 / 2 after `steps` steps
+ * from the current state, with respect to the body-force acceleration field
+ * set by hlbm_set_force_field (kind 1), by the discrete adjoint of the step
+ * (reverse streaming and the transposed Jacobian of the collision, Eqs. 2.2,
+ * 3.3, 4.4, 4.5) with checkpoint-and-recompute: a checkpoint every
+ * `ckpt_every` steps and one segment of recomputed states.  Body-force
+ * contexts only (HLBM_EUNSUPPORTED with H_i or F^SC).
+ *   workspace  caller-owned device memory, 256-byte aligned, of at least
+ *              hlbm_adjoint_workspace_bytes(ctx, steps, ckpt_every) bytes
+ *              (ceil(steps / ckpt_every) + ckpt_every - 1 states, two FP32
+ *              adjoint fields, reduction scratch)
+ *   dLdg       device [D][nz][ny][nx] FP32 output
+ *   loss       host output, L in FP64
+ * The context's state advances by `steps` (as hlbm_step would).  Synchronises. */
+size_t hlbm_adjoint_workspace_bytes(const hlbm_ctx* ctx, int steps, int ckpt_every);
+hlbm_status hlbm_adjoint_run(hlbm_ctx* ctx, int steps, int ckpt_every, void* workspace, size_t bytes, float* dLdg,
+                             double* loss);
+
 /* Quadrature of a lattice as compiled into the library: c[Q*3] (int),
  * w[Q], *cs2 = c0^2, returns Q (0 on bad lattice).  Any pointer may be NULL. */
 int hlbm_lattice_info(int lattice, int* c, double* w, double* cs2);

@@ -25,7 +25,8 @@ for _k, _v in STATUS.items():
 EXPORTS = ["hlbm_workspace_bytes", "hlbm_create", "hlbm_bind_memory", "hlbm_set_stream", "hlbm_get_stream",
            "hlbm_init", "hlbm_set_force_field", "hlbm_step", "hlbm_moments", "hlbm_diag", "hlbm_state_bytes",
            "hlbm_save", "hlbm_load", "hlbm_step_count", "hlbm_set_tile", "hlbm_synchronize", "hlbm_set_wait_timeout",
-           "hlbm_last_error", "hlbm_destroy", "hlbm_lattice_info", "hlbm_population_sums_noalloc"]
+           "hlbm_last_error", "hlbm_destroy", "hlbm_lattice_info", "hlbm_population_sums_noalloc",
+           "hlbm_adjoint_workspace_bytes", "hlbm_adjoint_run"]
 
 
 class hlbm_source_params(C.Structure):
@@ -70,6 +71,8 @@ _sigs = {
     "hlbm_destroy": ([_vp], _i),
     "hlbm_lattice_info": ([_i, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)], _i),
     "hlbm_population_sums_noalloc": ([_i, _ll, _i, _d, _vp, _vp, C.POINTER(C.c_double)], _i),
+    "hlbm_adjoint_workspace_bytes": ([_vp, _i, _i], _sz),
+    "hlbm_adjoint_run": ([_vp, _i, _i, _vp, _sz, _vp, C.POINTER(C.c_double)], _i),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)

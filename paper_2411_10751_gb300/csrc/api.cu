@@ -3,6 +3,7 @@
 // CUDA-graph replay of the step loop, diagnostics and checkpoints.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -625,6 +626,87 @@ hlbm_status hlbm_destroy(hlbm_ctx* c) {
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return HLBM_OK;
+}
+
+namespace {
+struct AdjLayout {
+  size_t state, nseg, nstates, off_lam0, off_lam1, off_part, total;
+};
+AdjLayout adj_layout(const hlbm_ctx* c, int steps, int K) {
+  AdjLayout L{};
+  L.state = align256((size_t)c->Q * (size_t)c->N * c->elem);
+  L.nseg = (size_t)((steps + K - 1) / K);
+  L.nstates = L.nseg + (size_t)(K - 1);  // checkpoints + recomputed states of one segment
+  const size_t lam = align256((size_t)c->Q * (size_t)c->N * 4);
+  L.off_lam0 = L.nstates * L.state;
+  L.off_lam1 = L.off_lam0 + lam;
+  L.off_part = L.off_lam1 + lam;
+  L.total = L.off_part + align256(((size_t)adjoint_seed_blocks(c->N) + 1) * 8 * sizeof(double));
+  return L;
+}
+}  // namespace
+
+size_t hlbm_adjoint_workspace_bytes(const hlbm_ctx* c, int steps, int ckpt_every) {
+  if (!c || steps < 1 || ckpt_every < 1) return 0;
+  return adj_layout(c, steps, std::min(ckpt_every, steps)).total;
+}
+
+hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* workspace, size_t bytes, float* dLdg,
+                             double* loss) {
+  hlbm_status st = usable(c);
+  if (st != HLBM_OK) return st;
+  if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
+  if (steps < 1 || ckpt_every < 1 || !workspace || !dLdg || !loss) return fail(c, HLBM_EINVAL, "bad adjoint arguments");
+  if (c->force_mode != FORCE_FIELD)
+    return fail(c, HLBM_EINVAL, "the gradient is taken with respect to a force field: call hlbm_set_force_field(kind 1)");
+  if (c->p.flags & (HLBM_SRC_H | HLBM_SRC_SC)) return fail(c, HLBM_EUNSUPPORTED, "the adjoint covers the body-force step");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return fail(c, HLBM_EINVAL, "workspace must be 256-byte aligned");
+  const int K = std::min(ckpt_every, steps);
+  const AdjLayout L = adj_layout(c, steps, K);
+  if (bytes < L.total) return fail(c, HLBM_ENOMEM, "adjoint workspace smaller than hlbm_adjoint_workspace_bytes()");
+  char* ws = static_cast<char*>(workspace);
+  auto state = [&](size_t k) { return static_cast<void*>(ws + k * L.state); };
+  float* lam[2] = {reinterpret_cast<float*>(ws + L.off_lam0), reinterpret_cast<float*>(ws + L.off_lam1)};
+  double* part = reinterpret_cast<double*>(ws + L.off_part);
+  const size_t sbytes = (size_t)c->Q * (size_t)c->N * c->elem;
+  const int thermal = (c->p.flags & HLBM_ISOTHERMAL) ? 0 : 1;
+  const float rho0 = (float)c->p.rho0, omega = (float)(1.0 / c->tau_hat), beta = (float)(1.0 - 0.5 / c->tau_hat);
+  // forward: checkpoint k is the state before step k K (its gather is f_{kK})
+  const int nseg = (int)L.nseg;
+  for (int k = 0; k < nseg; ++k) {
+    HLBM_CUDA(c, cudaMemcpyAsync(state(k), c->pop[c->cur], sbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    const int len = std::min(K, steps - k * K);
+    for (int j = 0; j < len; ++j) HLBM_CUDA(c, one_step(c), "forward step");
+    c->steps += len;
+  }
+  // seed from the final state: lambda_T, dL/dg at T, kinetic energy
+  HLBM_CUDA(c, launch_adjoint(c->lattice, c->storage, true, c->pop[c->cur], nullptr, lam[0], c->gfield, dLdg, part,
+                              c->N, c->nx, c->ny, c->nz, rho0, omega, beta, thermal, c->stream), "adjoint seed");
+  const int nb = adjoint_seed_blocks(c->N);
+  HLBM_CUDA(c, launch_reduce_partials(part, nb, part + (size_t)nb * 8, c->stream), "reduce");
+  int cur = 0;
+  // backward over segments: recompute the segment's states, then reverse steps
+  for (int k = nseg - 1; k >= 0; --k) {
+    const int len = std::min(K, steps - k * K);
+    // states of the segment: j = 0 is checkpoint k, j >= 1 are recomputed into slots nseg + j - 1
+    auto seg = [&](int j) { return j == 0 ? state(k) : state((size_t)nseg + j - 1); };
+    for (int j = 1; j < len; ++j) {
+      StepArgs a = make_args(c);
+      a.tma = 0;
+      a.fin = seg(j - 1);
+      a.fout = seg(j);
+      HLBM_CUDA(c, launch_step(c, a, false), "recompute step");
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      HLBM_CUDA(c, launch_adjoint(c->lattice, c->storage, false, seg(j), lam[cur], lam[cur ^ 1], c->gfield, dLdg,
+                                  nullptr, c->N, c->nx, c->ny, c->nz, rho0, omega, beta, thermal, c->stream),
+                "adjoint step");
+      cur ^= 1;
+    }
+  }
+  HLBM_CUDA(c, cudaMemcpyAsync(loss, part + (size_t)nb * 8, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+            "cudaMemcpyAsync");
+  return check_status(c);
 }
 
 int hlbm_lattice_info(int lattice, int* cvec, double* w, double* cs2) {

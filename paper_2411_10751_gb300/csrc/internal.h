@@ -76,4 +76,13 @@ cudaError_t launch_reduce_partials(const double* partials, int blocks, double* o
 // Number of CTAs a moments-mode launch with these sizes uses (size of the partials).
 int moment_blocks(int lattice, int nx, int ny, int nz);
 
+// Adjoint of the body-force step (adjoint.cu).  seed: lambda_T, dL/dg and
+// per-block kinetic-energy sums (adjoint_seed_blocks(N) blocks, stride 8) from
+// the state `fwd`; otherwise one reverse step lam_in -> lam_out with the
+// forward state `fwd` whose gather is f_n, accumulating dL/dg.
+cudaError_t launch_adjoint(int lattice, int storage, bool seed, const void* fwd, const float* lam_in, float* lam_out,
+                           const float* gfield, float* dLdg, double* partials, long long N, int nx, int ny, int nz,
+                           float rho0, float omega, float beta, int thermal, cudaStream_t s);
+int adjoint_seed_blocks(long long N);
+
 }  // namespace hlbm

@@ -152,6 +152,19 @@ class HLBM:
         """Schedule: rows per tile, nodes per thread, persistent (0 default, 1 off, 2 on)."""
         self._chk(abi.hlbm_set_tile(self.ctx, int(rows), int(nodes_per_thread), int(persistent)))
 
+    def adjoint(self, steps: int, ckpt_every: int = 50):
+        """(L, dL/dg): kinetic energy after `steps` steps from the current state and
+        its gradient with respect to the force field (a torch [D, ...] CUDA tensor)."""
+        nbytes = abi.hlbm_adjoint_workspace_bytes(self.ctx, int(steps), int(ckpt_every))
+        if nbytes == 0:
+            raise ValueError("steps and ckpt_every must be >= 1")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = torch.empty((self.D,) + self.shape, dtype=torch.float32, device=self.device)
+        loss = C.c_double()
+        self._chk(abi.hlbm_adjoint_run(self.ctx, int(steps), int(ckpt_every), C.c_void_p(ws.data_ptr()), nbytes,
+                                       C.c_void_p(grad.data_ptr()), C.byref(loss)))
+        return loss.value, grad
+
     def synchronize(self) -> None:
         self._chk(abi.hlbm_synchronize(self.ctx))
 
@@ -166,3 +179,22 @@ class HLBM:
             self.close()
         except Exception:
             pass
+
+
+class KineticEnergy(torch.autograd.Function):
+    """L(g) = sum rho |u|^2 / 2 after `steps` steps from the initial fields, as a
+    differentiable function of the acceleration field g [D, ...]; the gradient
+    comes from the adjoint kernels (hlbm_adjoint_run)."""
+
+    @staticmethod
+    def forward(ctx, g, solver: "HLBM", rho, u, theta, steps: int, ckpt_every: int = 50):
+        solver.init(rho, u, theta)
+        solver.set_force_field(g.detach(), "field")
+        loss, grad = solver.adjoint(steps, ckpt_every)
+        ctx.save_for_backward(grad)
+        return torch.tensor(loss, dtype=torch.float64, device=g.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (grad,) = ctx.saved_tensors
+        return (grad_out.to(grad.dtype) * grad, None, None, None, None, None, None)
