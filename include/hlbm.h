@@ -182,6 +182,21 @@ size_t hlbm_adjoint_workspace_bytes(const hlbm_ctx* ctx, int steps, int ckpt_eve
 hlbm_status hlbm_adjoint_run(hlbm_ctx* ctx, int steps, int ckpt_every, void* workspace, size_t bytes, float* dLdg,
                              double* loss);
 
+/* Batched step (D2Q37): advances many independent contexts -- any sizes,
+ * sources and parameters, one storage type -- together, with one kernel
+ * launch per time step over every tile of every domain (replayed from a CUDA
+ * graph).  The contexts must be initialised; hlbm_batch_create moves them onto
+ * the batch's stream, so their own calls stay ordered with batch steps.  Each
+ * context's state and step count advance as if hlbm_step had been called;
+ * hlbm_moments / hlbm_diag / hlbm_save work on them as usual.  A context must
+ * not be destroyed before the batch. */
+typedef struct hlbm_batch hlbm_batch;
+hlbm_status hlbm_batch_create(int n, hlbm_ctx* const* ctxs, hlbm_batch** out);
+hlbm_status hlbm_batch_step(hlbm_batch* batch, int n);
+hlbm_status hlbm_batch_synchronize(hlbm_batch* batch);
+void* hlbm_batch_get_stream(hlbm_batch* batch);
+hlbm_status hlbm_batch_destroy(hlbm_batch* batch);
+
 /* Quadrature of a lattice as compiled into the library: c[Q*3] (int),
  * w[Q], *cs2 = c0^2, returns Q (0 on bad lattice).  Any pointer may be NULL. */
 int hlbm_lattice_info(int lattice, int* c, double* w, double* cs2);

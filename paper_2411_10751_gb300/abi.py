@@ -26,7 +26,8 @@ EXPORTS = ["hlbm_workspace_bytes", "hlbm_create", "hlbm_bind_memory", "hlbm_set_
            "hlbm_init", "hlbm_set_force_field", "hlbm_step", "hlbm_moments", "hlbm_diag", "hlbm_state_bytes",
            "hlbm_save", "hlbm_load", "hlbm_step_count", "hlbm_set_tile", "hlbm_synchronize", "hlbm_set_wait_timeout",
            "hlbm_last_error", "hlbm_destroy", "hlbm_lattice_info", "hlbm_population_sums_noalloc",
-           "hlbm_adjoint_workspace_bytes", "hlbm_adjoint_run"]
+           "hlbm_adjoint_workspace_bytes", "hlbm_adjoint_run", "hlbm_batch_create", "hlbm_batch_step",
+           "hlbm_batch_synchronize", "hlbm_batch_get_stream", "hlbm_batch_destroy"]
 
 
 class hlbm_source_params(C.Structure):
@@ -73,6 +74,11 @@ _sigs = {
     "hlbm_population_sums_noalloc": ([_i, _ll, _i, _d, _vp, _vp, C.POINTER(C.c_double)], _i),
     "hlbm_adjoint_workspace_bytes": ([_vp, _i, _i], _sz),
     "hlbm_adjoint_run": ([_vp, _i, _i, _vp, _sz, _vp, C.POINTER(C.c_double)], _i),
+    "hlbm_batch_create": ([_i, C.POINTER(_vp), C.POINTER(_vp)], _i),
+    "hlbm_batch_step": ([_vp, _i], _i),
+    "hlbm_batch_synchronize": ([_vp], _i),
+    "hlbm_batch_get_stream": ([_vp], _vp),
+    "hlbm_batch_destroy": ([_vp], _i),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)

@@ -90,6 +90,12 @@ Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) 
   return L;
 }
 
+// v = hi + lo with hi = fl32(v), lo = fl32(v - hi)
+void split_ff(double v, float (&out)[2]) {
+  out[0] = (float)v;
+  out[1] = (float)(v - (double)out[0]);
+}
+
 hlbm_status fail(hlbm_ctx* c, hlbm_status st, const std::string& m, bool sticky = false) {
   if (c) {
     c->msg = m;
@@ -205,15 +211,15 @@ StepArgs make_args(const hlbm_ctx* c) {
   for (int d = 0; d < 3; ++d) a.g[d] = (float)c->p.force[d];
   a.h_coef = (c->p.flags & HLBM_SRC_H) ? (float)(1.0 - 1.0 / c->p.Pr) : 0.f;
   a.eos = c->p.eos;
-  a.eos_a = (float)c->p.eos_a;
-  a.eos_b = (float)c->p.eos_b;
-  a.eos_T = (float)c->p.eos_T;
+  const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
+  split_ff(2.0 * c->p.eos_a / cs2, a.psi_k1);
+  split_ff(2.0 * c->p.eos_T / cs2, a.psi_k2);
+  split_ff(c->p.eos == 0 ? c->p.eos_b : 0.25 * c->p.eos_b, a.psi_kb);
   a.status = c->status;
   a.tma = c->tma_ok ? 1 : 0;
   a.persistent = c->persistent;
   a.wait_ns = c->wait_ns;
   a.debug_skip_tma = c->debug_skip_tma;
-  const double cs2 = c->lattice == 0 ? D2Q37::cs2 : D3Q39::cs2;
   // sigma = -k c0^2 |F^SC|^2 / (D tau G psi^2), tau = tau^ - 1/2, G = -1 (Eq. 3.12, Table 2)
   a.p_coef = (c->p.flags & HLBM_SRC_P) ? (float)(c->p.k * cs2 / (c->D * (c->tau_hat - 0.5))) : 0.f;
   return a;
@@ -307,6 +313,32 @@ hlbm_status usable(hlbm_ctx* c) {
 }
 
 }  // namespace
+
+namespace hlbm {
+// accessors used by the batched step (batch.cu)
+bool ctx_batchable(const hlbm_ctx* c, int* storage, int* kind, int* nx, int* ny) {
+  if (!c || c->lattice != HLBM_D2Q37 || !c->initialised || c->failed) return false;
+  *storage = c->storage;
+  *kind = c->kind;
+  *nx = c->nx;
+  *ny = c->ny;
+  return true;
+}
+StepArgs ctx_step_args(hlbm_ctx* c, int parity) {
+  StepArgs a = make_args(c);
+  a.fin = c->pop[parity];
+  a.fout = c->pop[parity ^ 1];
+  a.tma_store = 0;
+  a.persistent = 0;
+  return a;
+}
+const CUtensorMap* ctx_tensor_map(hlbm_ctx* c, int buf, int wb, int hb) { return tensor_map(c, buf, wb, hb); }
+int ctx_cur(const hlbm_ctx* c) { return c->cur; }
+void ctx_advance(hlbm_ctx* c, int steps) {
+  c->cur ^= (steps & 1);
+  c->steps += steps;
+}
+}  // namespace hlbm
 
 extern "C" {
 

@@ -35,7 +35,10 @@ struct StepArgs {
   float g[3];             // uniform acceleration
   float h_coef;           // 1 - 1/Pr (H_i)
   int eos;                // 0 van der Waals, 1 Carnahan-Starling
-  float eos_a, eos_b, eos_T;
+  // psi^2 = 2 rho + k1 rho^2 - k2 rho Z(e), e = kb rho (float-float pairs hi, lo):
+  // k1 = 2 a / c0^2, k2 = 2 T / c0^2; vdW Z = 1 / (1 - e), kb = b;
+  // Carnahan-Starling Z = (1 + e + e^2 - e^3) / (1 - e)^3, kb = b / 4
+  float psi_k1[2], psi_k2[2], psi_kb[2];
   float p_coef;           // trace coefficient of P_i: sigma = p_coef |F^SC|^2 / psi^2
   int* status;            // device status word: set to HLBM_ETIMEOUT when a bounded wait expires
   int tma;                // 1: interior tiles are staged by TMA (input tensor map valid)

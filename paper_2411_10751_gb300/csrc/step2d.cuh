@@ -199,8 +199,8 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
     for (int k = 0; k < NPT; ++k)
       set_lane(g[i], k, to_float(sp[i * Cf::PLANE + (ty + k * TR + H) * Cf::WB + tx + H + Cf::rem(i)]));
   });
-  V dr, acc, J[3], Pih;
-  moments_h<L>(g, dr, acc, J, Pih);
+  V dr, dr_l, acc, J[3], Pih;
+  moments_h<L>(g, dr, dr_l, acc, J, Pih);
   const V rho = vadd(splat<V>(a.rho0), dr);
   V gax = splat<V>(0.f), gay = splat<V>(0.f);
 #pragma unroll
@@ -214,9 +214,12 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
   V sigma = splat<V>(0.f);
 
   if constexpr (KIND == KIND_SC) {
-    const V psi = vmap(rho, [&](float r) { return psi_of<L>(a, r); });
+    V psi;
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) aux[(ty + k * TR + H) * Fr::SW + tx + H] = lane(psi, k);
+    for (int k = 0; k < NPT; ++k) {
+      set_lane(psi, k, psi_of<L>(a, lane(dr, k), lane(dr_l, k)));
+      aux[(ty + k * TR + H) * Fr::SW + tx + H] = lane(psi, k);
+    }
     for (int k = tid; k < Fr::count; k += NT) {
       int i, j;
       Fr::pos(k, i, j);
@@ -225,7 +228,9 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
         constexpr int q = I;
         gh[q] = to_float(sp[q * Cf::PLANE + j * Cf::WB + i + Cf::rem(q)]);
       });
-      aux[j * Fr::SW + i] = psi_of<L>(a, a.rho0 + density_h<L>(gh));
+      float hl;
+      const float hd = density_h<L>(gh, hl);
+      aux[j * Fr::SW + i] = psi_of<L>(a, hd, hl);
     }
     __syncthreads();
     staged_done();
@@ -346,6 +351,8 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
     poly2<L>(s, a.omega, a.beta, K);
     const float om1 = 1.f - a.omega;
     K[0] = vfma(splat<V>(-om1), acc, K[0]);
+    // the density's rounding error matters where F^SC amplifies it
+    if constexpr (KIND == KIND_SC) K[0] = vadd(K[0], dr_l);
     apply_poly_h<L, 15>(g, K, om1, dr);
     if (TMA_STORE && a.tma_store) {
       // stage the tile's results densely in the (now unused) input planes and

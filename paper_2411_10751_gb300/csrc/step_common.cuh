@@ -174,8 +174,20 @@ __device__ __forceinline__ void gather(const typename C::T* __restrict__ f, long
 //   Pih = sum_i w_i |c_i|^2 (g_i - dr) = sum_{i>=1} w_i |c_i|^2 d_i - D c0^2 acc
 //       (= sum_i |c_i|^2 f^_i - rho D c0^2).
 // Opposite pairs share the sum and difference of their d.
+//
+// dr_l is the rounding error of dr = g_0 + acc (Knuth's two-sum).  That error
+// would reach all Q post-collision values of the node alike, i.e. act as a
+// density error, which the pseudopotential force amplifies at a liquid-gas
+// interface; with that force the collision adds dr_l back with the small
+// terms and psi takes the density as rho0 + dr + dr_l.
+template <class V>
+__device__ __forceinline__ V two_sum_err(V a, V b, V s) {
+  const V bb = vsub(s, a);
+  return vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
+}
+
 template <class L, class V>
-__device__ __forceinline__ void moments_h(V (&g)[L::Q], V& dr, V& acc, V (&J)[3], V& Pih) {
+__device__ __forceinline__ void moments_h(V (&g)[L::Q], V& dr, V& dr_l, V& acc, V (&J)[3], V& Pih) {
   const V g0 = g[0];
   V a = splat<V>(0.f), p = splat<V>(0.f);
   J[0] = J[1] = J[2] = splat<V>(0.f);
@@ -195,35 +207,93 @@ __device__ __forceinline__ void moments_h(V (&g)[L::Q], V& dr, V& acc, V (&J)[3]
   g[0] = splat<V>(0.f);
   acc = a;
   dr = vadd(g0, a);
+  dr_l = two_sum_err(g0, a, dr);
   Pih = vfma(splat<V>(-(float)(L::D * L::cs2)), a, p);
 }
 
-// dr alone, same summation (g is not modified).
 template <class L, class V>
-__device__ __forceinline__ V density_h(const V (&g)[L::Q]) {
+__device__ __forceinline__ void moments_h(V (&g)[L::Q], V& dr, V& acc, V (&J)[3], V& Pih) {
+  V dr_l;
+  moments_h<L>(g, dr, dr_l, acc, J, Pih);
+}
+
+// dr and dr_l alone, same summation (g is not modified).
+template <class L, class V>
+__device__ __forceinline__ V density_h(const V (&g)[L::Q], V& dr_l) {
   const V g0 = g[0];
   V a = splat<V>(0.f);
   static_for<L::NPAIR>([&](auto P) {
     constexpr int i = 2 * P + 1, j = 2 * P + 2;
     a = vfma(splat<V>((float)L::w(i)), vadd(vsub(g[i], g0), vsub(g[j], g0)), a);
   });
-  return vadd(g0, a);
+  const V dr = vadd(g0, a);
+  dr_l = two_sum_err(g0, a, dr);
+  return dr;
 }
 
 // ---------------------------------------------------------- pseudopotential
-// psi = sqrt(2 (p_EOS - rho c0^2) / (G c0^2)), G = -1, theta = 1 (Eq. 3.8)
+// psi = sqrt(2 (p_EOS - rho c0^2) / (G c0^2)), G = -1, theta = 1 (Eq. 3.8).
+// Written as psi^2 = 2 rho + k1 rho^2 - k2 rho Z(kb rho), the three terms
+// cancel to a few times less than the largest (and p_EOS - rho c0^2 before
+// them), and F^SC differences psi between neighbours, so a plain FP32
+// evaluation leaves psi noise of several ulp that F^SC turns into force noise
+// at the interface.  psi^2 is therefore formed in float-float arithmetic
+// (Dekker/Knuth error-free sum and FMA product) from the FP32 density, and
+// the square root takes one Newton correction: psi is within about half an
+// ulp of the value of the formula at the node's density.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ff_norm(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  const float s = __fadd_rn(x.h, y.h);
+  const float bb = __fsub_rn(s, x.h);
+  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(y.h, bb));
+  return ff_norm(s, __fadd_rn(e, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ ff ff_mul_f(ff x, float y) {
+  const float p = __fmul_rn(x.h, y);
+  return ff_norm(p, fmaf(x.l, y, fmaf(x.h, y, -p)));
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  const float p = __fmul_rn(x.h, y.h);
+  return ff_norm(p, fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p))));
+}
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+  const float q = __fdiv_rn(x.h, y.h);
+  const ff r = ff_add(x, ff_neg(ff_mul_f(y, q)));
+  return ff_norm(q, __fdiv_rn(r.h, y.h));
+}
+
+// The density enters as rho0 + dr + dr_l, formed exactly as a float-float.
 template <class L>
-__device__ __forceinline__ float psi_of(const StepArgs& a, float rho) {
-  float p;
+__device__ __forceinline__ float psi_of(const StepArgs& a, float dr, float dr_l) {
+  const float rh = __fadd_rn(a.rho0, dr);
+  const float bb = __fsub_rn(rh, a.rho0);
+  const float rl = __fadd_rn(__fsub_rn(a.rho0, __fsub_rn(rh, bb)), __fsub_rn(dr, bb));
+  const ff rho = ff_norm(rh, __fadd_rn(rl, dr_l));
+  const ff k1{a.psi_k1[0], a.psi_k1[1]}, k2{a.psi_k2[0], a.psi_k2[1]};
+  const ff e = ff_mul(ff{a.psi_kb[0], a.psi_kb[1]}, rho);
+  const ff one{1.f, 0.f};
+  const ff om = ff_add(one, ff_neg(e));
+  ff z;
   if (a.eos == 0) {
-    p = rho * a.eos_T / (1.f - a.eos_b * rho) - a.eos_a * rho * rho;
+    z = ff_div(rho, om);                                            // rho / (1 - e)
   } else {
-    const float e = 0.25f * a.eos_b * rho;
-    const float om = 1.f - e;
-    p = rho * a.eos_T * (1.f + e + e * e - e * e * e) / (om * om * om) - a.eos_a * rho * rho;
+    const ff e2 = ff_mul(e, e);
+    const ff num = ff_add(ff_add(ff_add(one, e), e2), ff_neg(ff_mul(e2, e)));
+    z = ff_div(ff_mul(num, rho), ff_mul(ff_mul(om, om), om));       // rho Z(e)
   }
-  const float s = (2.f / (float)L::cs2) * (rho * (float)L::cs2 - p);
-  return sqrtf(fmaxf(s, 0.f));
+  const ff quad = ff_mul(ff_add(ff{2.f, 0.f}, ff_mul(k1, rho)), rho);   // 2 rho + k1 rho^2
+  const ff s = ff_add(quad, ff_neg(ff_mul(k2, z)));
+  if (!(s.h > 0.f)) return 0.f;
+  const float h = __fsqrt_rn(s.h);
+  const float r = __fadd_rn(fmaf(-h, h, s.h), s.l);
+  return fmaf(r, __fdiv_rn(0.5f, h), h);
 }
 
 // ---------------------------------------------------------- body acceleration
@@ -401,10 +471,11 @@ __device__ __forceinline__ void apply_poly(float (&g)[L::Q], const float (&K)[NM
 
 
 // Collision in local-deviation form.  With d_i = g_i - g_0 and dr, acc from
-// moments_h, and K computed with B_00 = 0 and K_00 reduced by (1 - omega) acc,
+// moments_h, and K computed with B_00 = 0 and K_00 reduced by (1 - omega) acc
+// (and increased by dr_l with the pseudopotential force),
 //   g*_i = dr + [(1 - omega) d_i + P(c_i)]
-// equals (1 - omega) g_i + P_full(c_i) (P_full with B_00 = omega dr), but only
-// small numbers pass through the arithmetic before the final add of dr.
+// equals (1 - omega) g_i + P_full(c_i) (P_full with B_00 = omega (dr + dr_l)),
+// but only small numbers pass through the arithmetic before the final add of dr.
 template <class L, int NM, class V>
 __device__ __forceinline__ void apply_poly_h(V (&g)[L::Q], const V (&K)[NM], float om1, V dr) {
   const V o1 = splat<V>(om1);

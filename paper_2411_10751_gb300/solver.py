@@ -198,3 +198,35 @@ class KineticEnergy(torch.autograd.Function):
     def backward(ctx, grad_out):
         (grad,) = ctx.saved_tensors
         return (grad_out.to(grad.dtype) * grad, None, None, None, None, None, None)
+
+
+class Batch:
+    """Independent D2Q37 domains stepped together (hlbm_batch_*): one kernel
+    launch per time step over all tiles of all domains."""
+
+    def __init__(self, solvers: list):
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        b = C.c_void_p()
+        abi.check(abi.hlbm_batch_create(len(self.solvers), arr, C.byref(b)))
+        self.handle = b
+
+    def step(self, n: int = 1) -> None:
+        abi.check(abi.hlbm_batch_step(self.handle, int(n)))
+
+    def synchronize(self) -> None:
+        abi.check(abi.hlbm_batch_synchronize(self.handle))
+
+    def cuda_stream(self, device=0) -> torch.cuda.ExternalStream:
+        return torch.cuda.ExternalStream(abi.hlbm_batch_get_stream(self.handle), device=device)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            abi.hlbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -35,7 +35,7 @@ def _case3d(n=16, nx=None, ny=None, nz=None, Ma=0.1, amp=2e-4, seed=5):
         c.u = c.u[(slice(None),) + sl].copy()
         c.nz, c.ny, c.nx = c.rho.shape
     rng = np.random.default_rng(seed)
-    c.gfield = amp * (2 * rng.random((3,) + c.rho.shape) - 1)
+    c.gfield = W.fp32(amp * (2 * rng.random((3,) + c.rho.shape) - 1))
     return c
 
 
@@ -43,7 +43,7 @@ def _case2d(nx=40, ny=33, seed=6):
     c = W.thermal_decay(nx=nx, ny=ny, tau_hat=0.7, H=False, eps_T=0.02, u0=0.03)
     c.params["force"] = True
     rng = np.random.default_rng(seed)
-    c.gfield = 2e-4 * (2 * rng.random((2, ny, nx)) - 1)
+    c.gfield = W.fp32(2e-4 * (2 * rng.random((2, ny, nx)) - 1))
     return c
 
 

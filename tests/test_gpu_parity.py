@@ -133,7 +133,7 @@ def test_droplet_512_full_size(HLBM):
 def test_d3q39_taylor_green_parity(HLBM):
     c = W.taylor_green_3d(n=16, tau_hat=0.6, Ma=0.3)
     rng = np.random.default_rng(0)
-    c.gfield = 1e-5 * (2 * rng.random(c.gfield.shape) - 1)
+    c.gfield = W.fp32(1e-5 * (2 * rng.random(c.gfield.shape) - 1))
     mg, mo = run_pair(HLBM, c, 50)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
