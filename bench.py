@@ -10,7 +10,13 @@ ranks.  The population buffers (2 x 155 MB in FP32) are larger than the
 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|f16|bf16]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--schedule R,N,P] [--only-device]
+                  [--no-variants] [--no-extras] [--no-cpu-baseline]
+
+Besides the headline line fields, rank 0 reports the other storages
+(storage_variants), their errors against the FP64 oracle on a 256^2 copy,
+and two extras: the batched step over 256 uneven domains and the adjoint
+run on the 128^3 D3Q39 Taylor-Green case.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the host cores over a 256 x 256 sample of the same workload.
@@ -63,9 +69,10 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel_hash: str, storage: str):
+def _ncu_traffic(kernel_hash: str, storage: str, schedule):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if it was captured from the current kernel sources; else None."""
+    if it was captured from the current kernel sources with this schedule;
+    else None."""
     p = ROOT / "profiles" / "fused_step_thermal1024_dram.json"
     if not p.exists():
         return None
@@ -74,7 +81,7 @@ def _ncu_traffic(kernel_hash: str, storage: str):
     except ValueError:
         return None
     e = d.get(storage)
-    if not e or d.get("kernel_source_sha") != kernel_hash:
+    if not e or d.get("kernel_source_sha") != kernel_hash or list(e.get("schedule", [])) != list(schedule):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -253,6 +260,62 @@ def cpu_baseline(budget_s=12.0, n=1024):
             "sample": f"{k} FP64 oracle steps of the full {n}x{n} workload ({dt:.1f} s)"}
 
 
+def batched_extra(lrank, steps=100):
+    """Batched step: 256 independent Kolmogorov/droplet domains of sides
+    32..256 (hlbm_batch_*), device-resident, CUDA events on the batch stream."""
+    import torch
+    from paper_2411_10751_gb300.solver import HLBM, Batch
+    cases = W.batched(256, seed=0)
+    ctxs = []
+    for c in cases:
+        g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params, device=lrank)
+        if c.gfield is not None:
+            g.set_force_field(c.gfield[:, :, 0], "profile")
+        g.init(c.rho, c.u, c.theta)
+        ctxs.append(g)
+    b = Batch(ctxs)
+    b.step(4)
+    b.synchronize()
+    s = b.cuda_stream(lrank)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    b.step(steps)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    nodes = sum(c.nodes for c in cases)
+    b.close()
+    for g in ctxs:
+        g.close()
+    return {"workload": "256 periodic D2Q37 domains (Kolmogorov + H_i, vdW droplets), sides 32..256, FP32",
+            "nodes": nodes, "steps": steps, "launches": steps, "MLUPS": nodes * steps / (ms * 1e-3) / 1e6,
+            "achieved_GBs": 296 * nodes / (ms * 1e-3 / steps) / 1e9}
+
+
+def adjoint_extra(lrank, n=128, steps=400, ckpt=50):
+    """Adjoint of the body-force step on the D3Q39 Taylor-Green case: forward
+    run with checkpoints, recompute and reverse sweep (hlbm_adjoint_run)."""
+    import torch
+    from paper_2411_10751_gb300.solver import HLBM
+    c = W.taylor_green_3d(n=n, tau_hat=0.6, Ma=0.3, steps=steps)
+    g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, device=lrank)
+    g.set_force_field(c.gfield, "field")
+    g.init(c.rho, c.u, c.theta)
+    g.adjoint(4, 2)                      # warm-up of every kernel on the path
+    g.init(c.rho, c.u, c.theta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, grad = g.adjoint(steps, ckpt)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    g.close()
+    return {"workload": f"D3Q39 Taylor-Green {n}^3, Ma 0.3, tau 0.6: dL/dg of the kinetic energy at step {steps}, "
+                        f"checkpoint every {ckpt}",
+            "seconds": dt, "ms_per_reverse_step": dt * 1e3 / steps,
+            "MLUPS_reverse": c.nodes * steps / dt / 1e6, "loss": loss,
+            "note": "wall time of hlbm_adjoint_run: forward with checkpoints, segment recompute, reverse steps"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -287,7 +350,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint lines")
+    ap.add_argument("--schedule", default=None, help="rows,nodes_per_thread,persistent (skips the autotuner)")
+    ap.add_argument("--only-device", action="store_true",
+                    help="device-timed steps only (no e2e, variants, extras or CPU baseline; for profiling)")
     args = ap.parse_args()
+    if args.only_device:
+        args.no_variants = args.no_extras = args.no_cpu_baseline = True
     args.warmup = max(args.warmup, 3)
     ws, rank, lrank = _dist()
 
@@ -306,7 +375,10 @@ def main():
     pkg.load()
 
     case = W.thermal_decay(n=1024)
-    sched = tuned_schedule(case, args.storage, lrank)
+    if args.schedule:
+        sched = tuple(int(v) for v in args.schedule.split(","))
+    else:
+        sched = tuned_schedule(case, args.storage, lrank)
     ms, clocks, diag = time_device(case, args.storage, args.steps, args.warmup, ws, lrank, sched)
     ms = _max_over_ranks(ws, ms)
     nodes = case.nodes
@@ -318,13 +390,21 @@ def main():
     peak, peak_kind = _peaks()
     khash = _kernel_source_hash()
 
-    e2e_ms, h2d, d2h = time_e2e(case, args.storage, args.steps, ws, lrank, sched)
-    e2e_ms = _max_over_ranks(ws, e2e_ms)
+    e2e = None
+    if not args.only_device:
+        e2e_ms, h2d, d2h = time_e2e(case, args.storage, args.steps, ws, lrank, sched)
+        e2e_ms = _max_over_ranks(ws, e2e_ms)
+        e2e = {"value": nodes * args.steps * ws / (e2e_ms * 1e-3) / 1e6, "unit": METRIC,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "path": "hlbm_init(host) + hlbm_step(K) + hlbm_moments(host), pinned host buffers"}
 
     variants = None
     errors = None
     cpu = None
+    extras = None
     if rank == 0:
+        if not args.no_extras:
+            extras = {"batched": batched_extra(lrank), "adjoint": adjoint_extra(lrank)}
         if not args.no_variants:
             variants = {}
             for st in ("f32", "f16", "bf16"):
@@ -349,22 +429,24 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nodes_per_gpu": nodes, "storage": args.storage,
                        "schedule": {"rows": sched[0], "nodes_per_thread": sched[1],
-                                    "persistent": sched[2] == 2, "chosen_by": "autotune"},
+                                    "persistent": sched[2] == 2,
+                                    "chosen_by": "--schedule" if args.schedule else "autotune"},
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (2 x %d MB population buffers), no flush" %
                              (37 * elem * nodes // 2 ** 20)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": _ncu_traffic(khash, args.storage),
-                         "algorithmic_bytes_per_node": bytes_per_node, "kernel": "step2d_kernel (KIND_THERMAL)"},
-            "e2e": {"value": nodes * args.steps * ws / (e2e_ms * 1e-3) / 1e6, "unit": METRIC,
-                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "path": "hlbm_init(host) + hlbm_step(K) + hlbm_moments(host), pinned host buffers"},
+                         "traffic": _ncu_traffic(khash, args.storage, sched),
+                         "algorithmic_bytes_per_node": bytes_per_node,
+                         "kernel": ("step2d_persistent_kernel" if sched[2] == 2 else "step2d_kernel") +
+                                   f" (thermal kind, {sched[0]} rows, {sched[1]} nodes per thread)"},
+            "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "storage_variants": variants,
             "storage_error_vs_oracle": errors,
+            "extras": extras,
             "final_diag": [float(x) for x in diag],
             "kernel_source_sha": khash,
         }
