@@ -423,10 +423,62 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
   process_tile<ST, KIND, MOM, BY, NPT, true>(a, &tmap_out, smem, x0, y0, [] {});
 }
 
-// Persistent CTAs: each walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-// (row-major), and issues the next tile's boxes into the staging buffer as
-// soon as the current tile's last staged read is done, so the load overlaps
-// the current tile's collision and stores.
+// Tiles whose staging boxes lie inside the domain form a rectangle of tile
+// indices [ix0, ix1) x [iy0, iy1) (tile_boxed is monotone in x0 and y0); the
+// others, on the periodic edge, form a frame around it.
+template <class Cf, int BY>
+struct TileSplit {
+  int ntx, nty, ix0, ix1, iy0, iy1, ni, ne;
+  __device__ TileSplit(const StepArgs& a, bool tma) {
+    constexpr int H = Cf::H;
+    ntx = (a.nx + 31) / 32;
+    nty = (a.ny + BY - 1) / BY;
+    const int xl = H + 3 + (Cf::A - 1), xr = a.nx + H - 3 - Cf::WB;
+    const int yl = H + 3, yr = a.ny + H - 3 - Cf::HB;
+    ix0 = (xl + 31) / 32;
+    ix1 = xr >= 0 ? min(ntx, xr / 32 + 1) : 0;
+    iy0 = (yl + BY - 1) / BY;
+    iy1 = yr >= 0 ? min(nty, yr / BY + 1) : 0;
+    if (!tma || ix1 <= ix0 || iy1 <= iy0) ix0 = ix1 = iy0 = iy1 = 0;
+    ni = (ix1 - ix0) * (iy1 - iy0);
+    ne = ntx * nty - ni;
+  }
+  __device__ void interior(int j, int& tx, int& ty) const {
+    const int w = ix1 - ix0;
+    const int r = j / w;
+    ty = iy0 + r;
+    tx = ix0 + (j - r * w);
+  }
+  __device__ void edge(int e, int& tx, int& ty) const {
+    const int top = iy0 * ntx;
+    if (e < top) {
+      ty = e / ntx;
+      tx = e - ty * ntx;
+      return;
+    }
+    e -= top;
+    const int mw = ix0 + (ntx - ix1), mid = (iy1 - iy0) * mw;
+    if (e < mid) {
+      const int r = e / mw, cc = e - r * mw;
+      ty = iy0 + r;
+      tx = cc < ix0 ? cc : ix1 + (cc - ix0);
+      return;
+    }
+    e -= mid;
+    const int r = e / ntx;
+    ty = iy1 + r;
+    tx = e - r * ntx;
+  }
+};
+
+// Persistent CTAs.  CTA b takes the edge tiles G-1-b, 2G-1-b, ... (G CTAs;
+// edge tiles are staged by per-node gathers) first and then the interior
+// tiles b, b+G, ... in row-major order; while it works on a tile it already
+// stages the next interior tile (TMA boxes issued as soon as the current
+// tile's last staged read is done), so after its edge tiles the loads overlap
+// the collision and stores without a break.  Handing the edge tiles to the
+// CTAs from the top evens out the work (the low CTAs take one more interior
+// tile when the interior count is not a multiple of G).
 template <int ST, int KIND, int BY, int NPT>
 __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY, NPT>()))
     step2d_persistent_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap) {
@@ -436,29 +488,33 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
   typename Cf::T* sp = reinterpret_cast<typename Cf::T*>(smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int ntx = (a.nx + 31) / 32;
-  const int ntiles = ntx * ((a.ny + BY - 1) / BY);
   const bool aligned = (smem_u32(smem) & 127u) == 0;
+  const TileSplit<Cf, BY> ts(a, a.tma && aligned);
+  const int G = gridDim.x, b = blockIdx.x;
+  const int e0 = G - 1 - b;
+  const int ne = ts.ne > e0 ? (ts.ne - e0 + G - 1) / G : 0;
+  const int ni = ts.ni > b ? (ts.ni - b + G - 1) / G : 0;
+  auto origin = [&](int p, int& x0, int& y0) {
+    int tx, ty;
+    if (p < ne) ts.edge(e0 + p * G, tx, ty);
+    else ts.interior(b + (p - ne) * G, tx, ty);
+    x0 = tx * 32;
+    y0 = ty * BY;
+  };
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
   uint32_t phase = 0;
-  int t = blockIdx.x;
-  auto origin = [&](int tt, int& x0, int& y0) {
-    const int by = tt / ntx;
-    x0 = (tt - by * ntx) * 32;
-    y0 = by * BY;
-  };
-  if (t < ntiles && tid == 0) {
+  if (ne + ni > 0 && tid == 0) {
     int x0, y0;
-    origin(t, x0, y0);
+    origin(0, x0, y0);
     if (aligned && tile_boxed<Cf>(a, x0, y0)) issue_tile<Cf>(sp, &tmap, bar, x0, y0, a.debug_skip_tma);
   }
-  for (; t < ntiles; t += gridDim.x) {
+  for (int p = 0; p < ne + ni; ++p) {
     int x0, y0;
-    origin(t, x0, y0);
+    origin(p, x0, y0);
     if (aligned && tile_boxed<Cf>(a, x0, y0)) {
       const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
       if (!__syncthreads_and(ok)) {
@@ -472,11 +528,11 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
       __syncthreads();
     }
-    const int tn = t + gridDim.x;
+    const int pn = p + 1;
     process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, [&] {
-      if (tid == 0 && tn < ntiles) {
+      if (tid == 0 && pn < ne + ni) {
         int xn, yn;
-        origin(tn, xn, yn);
+        origin(pn, xn, yn);
         if (aligned && tile_boxed<Cf>(a, xn, yn)) {
           fence_proxy_async_smem();
           issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma);
