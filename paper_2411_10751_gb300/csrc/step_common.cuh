@@ -476,9 +476,93 @@ __device__ __forceinline__ void apply_poly(float (&g)[L::Q], const float (&K)[NM
 //   g*_i = dr + [(1 - omega) d_i + P(c_i)]
 // equals (1 - omega) g_i + P_full(c_i) (P_full with B_00 = omega (dr + dr_l)),
 // but only small numbers pass through the arithmetic before the final add of dr.
+//
+// On D2Q37 the polynomial is evaluated per symmetry class: for a = |c_x|,
+// b = |c_y| and signs s_x, s_y,
+//   P(c) = S(a, b) + s_x s_y T(a, b) + s_x OA(a, b) + s_y OB(a, b),
+//   S  = K00 + a^2 K20 + b^2 K02 + a^4 K40 + a^2 b^2 K22 + b^4 K04,
+//   T  = a b K11 + a^3 b K31 + a b^3 K13,
+//   OA = a K10 + a^3 K30 + a b^2 K12,   OB = b K01 + a^2 b K21 + b^3 K03,
+// so S, T, OA, OB are formed once for the (up to) four velocities of a class
+// and each opposite pair shares its even part.
+template <class V>
+__device__ __forceinline__ V vfma_c(float c, V x, V acc) {
+  if (c == 1.f) return vadd(acc, x);
+  return vfma(splat<V>(c), x, acc);
+}
+
+template <class L, class V>
+__device__ __forceinline__ void apply_poly_h2(V (&g)[L::Q], const V (&K)[15], V o1, V dr) {
+  constexpr int M00 = mono2_index(0, 0), M10 = mono2_index(1, 0), M01 = mono2_index(0, 1);
+  constexpr int M20 = mono2_index(2, 0), M11 = mono2_index(1, 1), M02 = mono2_index(0, 2);
+  constexpr int M30 = mono2_index(3, 0), M21 = mono2_index(2, 1), M12 = mono2_index(1, 2), M03 = mono2_index(0, 3);
+  constexpr int M40 = mono2_index(4, 0), M31 = mono2_index(3, 1), M22 = mono2_index(2, 2), M13 = mono2_index(1, 3);
+  constexpr int M04 = mono2_index(0, 4);
+  g[0] = vadd(dr, K[M00]);
+  // classes (a, b) = (|c_x|, |c_y|) of the pair representatives
+  static_for<4>([&](auto Aa) {
+    static_for<4>([&](auto Bb) {
+      constexpr int a = Aa, b = Bb;
+      constexpr bool used = [] {
+        for (int p = 0; p < L::NPAIR; ++p) {
+          const int cx = L::c(2 * p + 1, 0), cy = L::c(2 * p + 1, 1);
+          if ((cx < 0 ? -cx : cx) == a && (cy < 0 ? -cy : cy) == b) return true;
+        }
+        return false;
+      }();
+      if constexpr (used && (a + b) > 0) {
+        constexpr float a2 = (float)(a * a), b2 = (float)(b * b), ab = (float)(a * b);
+        V S = K[M00];
+        if constexpr (a > 0) S = vfma_c(a2 * a2, K[M40], vfma_c(a2, K[M20], S));
+        if constexpr (b > 0) S = vfma_c(b2 * b2, K[M04], vfma_c(b2, K[M02], S));
+        if constexpr (a > 0 && b > 0) S = vfma_c(a2 * b2, K[M22], S);
+        V T = splat<V>(0.f), OA = splat<V>(0.f), OB = splat<V>(0.f);
+        if constexpr (a > 0 && b > 0)
+          T = vmul(splat<V>(ab), vfma_c(b2, K[M13], vfma_c(a2, K[M31], K[M11])));
+        if constexpr (a > 0) {
+          V t = vfma_c(a2, K[M30], K[M10]);
+          if constexpr (b > 0) t = vfma_c(b2, K[M12], t);
+          OA = (a == 1) ? t : vmul(splat<V>((float)a), t);
+        }
+        if constexpr (b > 0) {
+          V t = vfma_c(b2, K[M03], K[M01]);
+          if constexpr (a > 0) t = vfma_c(a2, K[M21], t);
+          OB = (b == 1) ? t : vmul(splat<V>((float)b), t);
+        }
+        static_for<L::NPAIR>([&](auto P) {
+          constexpr int i = 2 * P + 1, j = 2 * P + 2;
+          constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
+          if constexpr ((cx < 0 ? -cx : cx) == a && (cy < 0 ? -cy : cy) == b) {
+            constexpr int sx = cx > 0 ? 1 : (cx < 0 ? -1 : 0), sy = cy > 0 ? 1 : (cy < 0 ? -1 : 0);
+            V E, O;   // even part, odd part at c_i
+            if constexpr (sx * sy > 0) E = vadd(S, T);
+            else if constexpr (sx * sy < 0) E = vsub(S, T);
+            else E = S;
+            if constexpr (sy == 0) O = OA;
+            else if constexpr (sx == 0) O = OB;
+            else if constexpr (sx == sy) O = vadd(OA, OB);
+            else O = vsub(OA, OB);
+            constexpr bool flip = (sx < 0) || (sx == 0 && sy < 0);   // O above is -(odd part at c_i)
+            if constexpr (!flip) {
+              g[i] = vadd(dr, vfma(o1, g[i], vadd(E, O)));
+              g[j] = vadd(dr, vfma(o1, g[j], vsub(E, O)));
+            } else {
+              g[i] = vadd(dr, vfma(o1, g[i], vsub(E, O)));
+              g[j] = vadd(dr, vfma(o1, g[j], vadd(E, O)));
+            }
+          }
+        });
+      }
+    });
+  });
+}
+
 template <class L, int NM, class V>
 __device__ __forceinline__ void apply_poly_h(V (&g)[L::Q], const V (&K)[NM], float om1, V dr) {
   const V o1 = splat<V>(om1);
+  if constexpr (NM == 15 && L::D == 2) {
+    apply_poly_h2<L>(g, K, o1, dr);
+  } else {
   g[0] = vadd(dr, K[0]);
   static_for<L::NPAIR>([&](auto P) {
     constexpr int i = 2 * P + 1, j = 2 * P + 2;
@@ -514,6 +598,7 @@ __device__ __forceinline__ void apply_poly_h(V (&g)[L::Q], const V (&K)[NM], flo
     g[i] = vadd(dr, vfma(o1, g[i], vadd(E, O)));
     g[j] = vadd(dr, vfma(o1, g[j], vsub(E, O)));
   });
+  }
 }
 
 }  // namespace hlbm
