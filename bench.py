@@ -150,9 +150,15 @@ def _max_over_ranks(ws, x: float) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard(n_items: int, rank: int, ws: int) -> list[int]:
+    """Round-robin share of n independent items for this rank."""
+    return list(range(rank, n_items, ws))
 
 
 def tuned_schedule(case, storage, lrank):
@@ -260,12 +266,15 @@ def cpu_baseline(budget_s=12.0, n=1024):
             "sample": f"{k} FP64 oracle steps of the full {n}x{n} workload ({dt:.1f} s)"}
 
 
-def batched_extra(lrank, steps=100):
+def batched_extra(lrank, ws=1, rank=0, steps=100):
     """Batched step: 256 independent Kolmogorov/droplet domains of sides
-    32..256 (hlbm_batch_*), device-resident, CUDA events on the batch stream."""
+    32..256 (hlbm_batch_*), device-resident, CUDA events on the batch stream.
+    With several ranks each steps its round-robin share of the domains (no
+    data exchange); the time is the maximum over ranks."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM, Batch
-    cases = W.batched(256, seed=0)
+    all_cases = W.batched(256, seed=0)
+    cases = [all_cases[k] for k in shard(len(all_cases), rank, ws)]
     ctxs = []
     for c in cases:
         g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params, device=lrank)
@@ -278,18 +287,20 @@ def batched_extra(lrank, steps=100):
     b.synchronize()
     s = b.cuda_stream(lrank)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
     e0.record(s)
     b.step(steps)
     e1.record(s)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    nodes = sum(c.nodes for c in cases)
+    _barrier(ws)
+    ms = _max_over_ranks(ws, e0.elapsed_time(e1))
+    nodes = sum(c.nodes for c in all_cases)
     b.close()
     for g in ctxs:
         g.close()
     return {"workload": "256 periodic D2Q37 domains (Kolmogorov + H_i, vdW droplets), sides 32..256, FP32",
-            "nodes": nodes, "steps": steps, "launches": steps, "MLUPS": nodes * steps / (ms * 1e-3) / 1e6,
-            "achieved_GBs": 296 * nodes / (ms * 1e-3 / steps) / 1e9}
+            "nodes": nodes, "steps": steps, "launches_per_rank": steps, "ranks": ws,
+            "MLUPS": nodes * steps / (ms * 1e-3) / 1e6, "achieved_GBs": 296 * nodes / (ms * 1e-3 / steps) / 1e9}
 
 
 def adjoint_extra(lrank, n=128, steps=400, ckpt=50):
@@ -402,9 +413,11 @@ def main():
     errors = None
     cpu = None
     extras = None
+    if not args.no_extras:
+        extras = {"batched": batched_extra(lrank, ws, rank)}
+        if rank == 0:
+            extras["adjoint"] = adjoint_extra(lrank)
     if rank == 0:
-        if not args.no_extras:
-            extras = {"batched": batched_extra(lrank), "adjoint": adjoint_extra(lrank)}
         if not args.no_variants:
             variants = {}
             for st in ("f32", "f16", "bf16"):
