@@ -61,6 +61,8 @@ struct hlbm_ctx {
   };
   std::vector<TMap> tmaps;
   int* status = nullptr;          // device status word (bounded waits)
+  unsigned long long* tile_ctr = nullptr;  // persistent step's tile counter
+  bool ctr_reset = true;          // the counter must be zeroed before the next step
   unsigned long long wait_ns = 2000000000ull;
   int debug_skip_tma = 0;
 };
@@ -179,6 +181,7 @@ void carve(hlbm_ctx* c) {
   c->partials = reinterpret_cast<double*>(c->arena + L.off_part);
   c->red = reinterpret_cast<double*>(c->arena + L.off_red);
   c->status = reinterpret_cast<int*>(c->arena + L.off_red + 64);
+  c->tile_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 128);
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -218,6 +221,7 @@ StepArgs make_args(const hlbm_ctx* c) {
   a.status = c->status;
   a.tma = c->tma_ok ? 1 : 0;
   a.persistent = c->persistent;
+  a.tile_ctr = c->tile_ctr;
   a.wait_ns = c->wait_ns;
   a.debug_skip_tma = c->debug_skip_tma;
   // sigma = -k c0^2 |F^SC|^2 / (D tau G psi^2), tau = tau^ - 1/2, G = -1 (Eq. 3.12, Table 2)
@@ -446,6 +450,7 @@ hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float
     a.theta = stage + (1 + c->D) * n;
   }
   cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = launch_init(c->lattice, a, c->storage, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);  // host buffers are borrowed
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
@@ -483,6 +488,11 @@ hlbm_status hlbm_step(hlbm_ctx* c, int n) {
   if (st != HLBM_OK) return st;
   if (n < 0) return fail(c, HLBM_EINVAL, "n must be >= 0");
   if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
+  if (c->ctr_reset) {
+    // the persistent launch's CTA count may have changed: restart the counter
+    HLBM_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
+    c->ctr_reset = false;
+  }
   while (n >= kGraphSteps) {
     cudaGraphExec_t& ge = c->graph[c->cur];
     if (!ge) {
@@ -608,6 +618,7 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
   HLBM_CUDA(c, cudaMemcpyAsync(c->pop[0], static_cast<const char*>(host_buf) + 64, (size_t)c->Q * c->N * c->elem,
                                cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "cudaMemsetAsync");
+  HLBM_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   c->cur = 0;
   c->steps = hdr[6];
@@ -629,6 +640,7 @@ hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread, int persi
   c->rows = rows;
   c->npt = nodes_per_thread;
   c->persistent = (persistent == 2) ? 1 : 0;
+  c->ctr_reset = true;
   drop_graphs(c);
   return HLBM_OK;
 }

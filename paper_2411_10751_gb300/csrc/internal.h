@@ -44,6 +44,7 @@ struct StepArgs {
   int tma;                // 1: interior tiles are staged by TMA (input tensor map valid)
   int tma_store;          // 1: results are written by TMA (output tensor map valid)
   int persistent;         // 1: persistent CTAs that prefetch their next tile (2D step)
+  unsigned long long* tile_ctr;  // persistent step: tile counter; each launch takes exactly tiles + CTAs values
   unsigned long long wait_ns;  // wall-time limit of a bounded mbarrier wait
   int debug_skip_tma;     // test hook: arm the barrier but issue no copy (the wait must expire)
 };

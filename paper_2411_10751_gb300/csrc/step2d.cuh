@@ -471,50 +471,61 @@ struct TileSplit {
   }
 };
 
-// Persistent CTAs.  CTA b takes the edge tiles G-1-b, 2G-1-b, ... (G CTAs;
-// edge tiles are staged by per-node gathers) first and then the interior
-// tiles b, b+G, ... in row-major order; while it works on a tile it already
-// stages the next interior tile (TMA boxes issued as soon as the current
-// tile's last staged read is done), so after its edge tiles the loads overlap
-// the collision and stores without a break.  Handing the edge tiles to the
-// CTAs from the top evens out the work (the low CTAs take one more interior
-// tile when the interior count is not a multiple of G).
+// Persistent CTAs that take tiles in a global order from a device counter:
+// first the periodic-edge tiles (staged by per-node gathers), then the
+// interior tiles row by row.  While a CTA works on a tile it already takes
+// the next index and stages that tile by TMA as soon as the current tile's
+// last staged read is done, so loads overlap the collision and stores; and
+// since tiles are handed out in order, the tiles in flight stay a compact
+// band of the domain (their frames are served by L2) however the CTAs' speeds
+// differ.  The counter is never reset between launches: a launch of G CTAs
+// over T tiles takes exactly T + G values (every CTA stops at its first index
+// >= T), so the tile is the counter value mod (T + G).
 template <int ST, int KIND, int BY, int NPT>
 __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY, NPT>()))
     step2d_persistent_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap) {
   using Cf = Cfg2<ST, KIND, false, BY>;
   constexpr int NT = 32 * BY / NPT;
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_next;
   typename Cf::T* sp = reinterpret_cast<typename Cf::T*>(smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const bool aligned = (smem_u32(smem) & 127u) == 0;
   const TileSplit<Cf, BY> ts(a, a.tma && aligned);
-  const int G = gridDim.x, b = blockIdx.x;
-  const int e0 = G - 1 - b;
-  const int ne = ts.ne > e0 ? (ts.ne - e0 + G - 1) / G : 0;
-  const int ni = ts.ni > b ? (ts.ni - b + G - 1) / G : 0;
-  auto origin = [&](int p, int& x0, int& y0) {
+  const int ntiles = ts.ntx * ts.nty;
+  const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
+  auto origin = [&](int t, int& x0, int& y0) {
     int tx, ty;
-    if (p < ne) ts.edge(e0 + p * G, tx, ty);
-    else ts.interior(b + (p - ne) * G, tx, ty);
+    if (t < ts.ne) ts.edge(t, tx, ty);
+    else ts.interior(t - ts.ne, tx, ty);
     x0 = tx * 32;
     y0 = ty * BY;
+  };
+  // tid 0: takes the next tile index and, if it is a boxed tile, stages it
+  auto take_and_issue = [&]() {
+    const int tn = (int)(atomicAdd(a.tile_ctr, 1ull) % period);
+    s_next = tn;
+    if (tn < ntiles) {
+      int xn, yn;
+      origin(tn, xn, yn);
+      if (aligned && tile_boxed<Cf>(a, xn, yn)) {
+        fence_proxy_async_smem();
+        issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma);
+      }
+    }
   };
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    take_and_issue();
   }
   __syncthreads();
   uint32_t phase = 0;
-  if (ne + ni > 0 && tid == 0) {
+  int t = s_next;
+  while (t < ntiles) {
     int x0, y0;
-    origin(0, x0, y0);
-    if (aligned && tile_boxed<Cf>(a, x0, y0)) issue_tile<Cf>(sp, &tmap, bar, x0, y0, a.debug_skip_tma);
-  }
-  for (int p = 0; p < ne + ni; ++p) {
-    int x0, y0;
-    origin(p, x0, y0);
+    origin(t, x0, y0);
     if (aligned && tile_boxed<Cf>(a, x0, y0)) {
       const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
       if (!__syncthreads_and(ok)) {
@@ -528,18 +539,11 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
       __syncthreads();
     }
-    const int pn = p + 1;
     process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, [&] {
-      if (tid == 0 && pn < ne + ni) {
-        int xn, yn;
-        origin(pn, xn, yn);
-        if (aligned && tile_boxed<Cf>(a, xn, yn)) {
-          fence_proxy_async_smem();
-          issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma);
-        }
-      }
+      if (tid == 0) take_and_issue();
     });
-    __syncthreads();  // the shared aux tile is reused by the next tile
+    __syncthreads();  // s_next is published; the shared aux tile is reused by the next tile
+    t = s_next;
   }
 }
 
