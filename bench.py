@@ -43,6 +43,25 @@ sys.path.insert(0, str(ROOT))
 import workloads as W  # noqa: E402
 
 WORKLOAD = "D2Q37 thermal decay + H_i (Pr=0.71), 1024x1024 periodic, tau=0.7"
+# other forward workloads (--workload, and the forward_sweep extra)
+WORKLOADS = {
+    "thermal1024": (lambda: W.thermal_decay(n=1024), WORKLOAD),
+    "kolmogorov2048": (lambda: W.kolmogorov(2048), "D2Q37 Kolmogorov flow, 2048x2048 periodic, tau=0.8, g=1e-5"),
+    "kolmogorov4096": (lambda: W.kolmogorov(4096), "D2Q37 Kolmogorov flow, 4096x4096 periodic, tau=0.8, g=1e-5"),
+    "tg3d128": (lambda: W.taylor_green_3d(n=128), "D3Q39 compressible Taylor-Green 128^3, Ma=0.3, tau=0.6, body force"),
+}
+
+
+def _bytes_per_node(case, storage):
+    return 2 * (37 if case.lattice == "D2Q37" else 39) * (4 if storage == "f32" else 2)
+
+
+def _set_force(g, case):
+    if case.gfield is not None:
+        if case.lattice == "D2Q37":
+            g.set_force_field(case.gfield[:, :, 0], "profile")
+        else:
+            g.set_force_field(case.gfield, "field")
 METRIC = "MLUPS"
 
 
@@ -165,18 +184,38 @@ def tuned_schedule(case, storage, lrank):
     """Autotuned (rows, nodes per thread, persistent) for this workload (untimed)."""
     import torch
     from paper_2411_10751_gb300 import autotune
+    force, kind = None, None
+    if case.gfield is not None:
+        force, kind = (case.gfield[:, :, 0], "profile") if case.lattice == "D2Q37" else (case.gfield, "field")
     with torch.cuda.device(lrank):
         return autotune.tune(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params,
-                             case.rho, case.u, case.theta, storage=storage)
+                             case.rho, case.u, case.theta, storage=storage, force=force, force_kind=kind)
+
+
+def forward_sweep(lrank, steps=400, warmup=20):
+    """The other forward configurations judged against the HBM roofline: the
+    Kolmogorov flow at 2048^2 and 4096^2 and the D3Q39 Taylor-Green 128^3 step."""
+    peak, kind = _peaks()
+    out = []
+    for name in ("kolmogorov2048", "kolmogorov4096", "tg3d128"):
+        case = WORKLOADS[name][0]()
+        sched = tuned_schedule(case, "f32", lrank)
+        ms, _, _ = time_device(case, "f32", steps, warmup, 1, lrank, sched)
+        mlups = case.nodes * steps / (ms * 1e-3) / 1e6
+        gbs = _bytes_per_node(case, "f32") * mlups / 1e3
+        out.append({"workload": WORKLOADS[name][1], "storage": "f32", "schedule": list(sched), "MLUPS": mlups,
+                    "achieved_GBs": gbs, "frac_of_" + kind: gbs / peak})
+    return out
 
 
 def time_device(case, storage, steps, warmup, ws, lrank, schedule=None):
     """Device-resident run: K steps timed with CUDA events on the context's stream."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM
-    g = HLBM(case.lattice, case.nx, case.ny, 1, case.tau_hat, case.params, storage=storage, device=lrank)
+    g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage, device=lrank)
     if schedule:
         g.set_tile(*schedule)
+    _set_force(g, case)
     g.init(case.rho, case.u, case.theta)
     g.step(warmup)
     g.synchronize()
@@ -203,9 +242,10 @@ def time_e2e(case, storage, steps, ws, lrank, schedule=None):
     (H2D), K steps, hlbm_moments to pinned host buffers (D2H); wall time."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM
-    g = HLBM(case.lattice, case.nx, case.ny, 1, case.tau_hat, case.params, storage=storage, device=lrank)
+    g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage, device=lrank)
     if schedule:
         g.set_tile(*schedule)
+    _set_force(g, case)
     pin = {k: torch.from_numpy(np.asarray(getattr(case, k), np.float32)).pin_memory() for k in ("rho", "u", "theta")}
     out = {k: torch.empty_like(pin[k]).pin_memory() for k in pin}
     g.init(pin["rho"].numpy(), pin["u"].numpy(), pin["theta"].numpy())   # warm-up of the path
@@ -363,6 +403,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint lines")
     ap.add_argument("--schedule", default=None, help="rows,nodes_per_thread,persistent (skips the autotuner)")
+    ap.add_argument("--workload", default="thermal1024", choices=sorted(WORKLOADS),
+                    help="forward workload of the line (default: the 1024^2 thermal-decay benchmark)")
     ap.add_argument("--only-device", action="store_true",
                     help="device-timed steps only (no e2e, variants, extras or CPU baseline; for profiling)")
     args = ap.parse_args()
@@ -385,7 +427,7 @@ def main():
     _barrier(ws)
     pkg.load()
 
-    case = W.thermal_decay(n=1024)
+    case = WORKLOADS[args.workload][0]()
     if args.schedule:
         sched = tuple(int(v) for v in args.schedule.split(","))
     else:
@@ -395,7 +437,7 @@ def main():
     nodes = case.nodes
     value = nodes * args.steps * ws / (ms * 1e-3) / 1e6
     elem = 4 if args.storage == "f32" else 2
-    bytes_per_node = 2 * 37 * elem
+    bytes_per_node = _bytes_per_node(case, args.storage)
     launch_s = ms * 1e-3 / args.steps
     achieved = bytes_per_node * nodes / launch_s / 1e9
     peak, peak_kind = _peaks()
@@ -417,6 +459,7 @@ def main():
         extras = {"batched": batched_extra(lrank, ws, rank)}
         if rank == 0:
             extras["adjoint"] = adjoint_extra(lrank)
+            extras["forward_sweep"] = forward_sweep(lrank)
     if rank == 0:
         if not args.no_variants:
             variants = {}
@@ -428,9 +471,10 @@ def main():
                 vms, _, _ = time_device(case, st, k, args.warmup, 1, lrank, vsched)
                 e = 4 if st == "f32" else 2
                 variants[st] = {"MLUPS": nodes * k / (vms * 1e-3) / 1e6, "schedule": list(vsched),
-                                "achieved_GBs": 2 * 37 * e * nodes / (vms * 1e-3 / k) / 1e9,
-                                "frac_of_" + peak_kind: 2 * 37 * e * nodes / (vms * 1e-3 / k) / 1e9 / peak}
-            errors = storage_errors()
+                                "achieved_GBs": _bytes_per_node(case, st) * nodes / (vms * 1e-3 / k) / 1e9,
+                                "frac_of_" + peak_kind: _bytes_per_node(case, st) * nodes / (vms * 1e-3 / k) / 1e9 / peak}
+            if args.workload == "thermal1024":
+                errors = storage_errors()
         if not args.no_cpu_baseline:
             cpu = cpu_baseline()
 
@@ -440,19 +484,20 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes_per_gpu": nodes, "storage": args.storage,
+            "config": {"workload": WORKLOADS[args.workload][1], "nodes_per_gpu": nodes, "storage": args.storage,
                        "schedule": {"rows": sched[0], "nodes_per_thread": sched[1],
                                     "persistent": sched[2] == 2,
                                     "chosen_by": "--schedule" if args.schedule else "autotune"},
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (2 x %d MB population buffers), no flush" %
-                             (37 * elem * nodes // 2 ** 20)},
+                             (bytes_per_node // 2 * nodes // 2 ** 20)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _ncu_traffic(khash, args.storage, sched),
                          "algorithmic_bytes_per_node": bytes_per_node,
-                         "kernel": ("step2d_persistent_kernel" if sched[2] == 2 else "step2d_kernel") +
-                                   f" (thermal kind, {sched[0]} rows, {sched[1]} nodes per thread)"},
+                         "kernel": ("step3d_kernel" if case.lattice == "D3Q39" else
+                                    ("step2d_persistent_kernel" if sched[2] == 2 else "step2d_kernel")) +
+                                   f" ({sched[0]} rows, {sched[1]} nodes per thread)"},
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,

@@ -272,7 +272,7 @@ const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
 }
 
 cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
-  if (c->lattice != 0) return launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->stream);
+  if (c->lattice != 0) return launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->npt, c->stream);
   CUtensorMap maps[2];
   std::memset(maps, 0, sizeof(maps));
   a.tma_store = 0;
