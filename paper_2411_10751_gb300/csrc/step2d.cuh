@@ -471,9 +471,12 @@ struct TileSplit {
   }
 };
 
-// Persistent CTAs that take tiles in a global order from a device counter:
-// first the periodic-edge tiles (staged by per-node gathers), then the
-// interior tiles row by row.  While a CTA works on a tile it already takes
+// Persistent CTAs that take tiles in a global order from a device counter.
+// Tiles on the periodic edge stage by per-node gathers, synchronously; when
+// they are more than 5% of the tiles they come first (their stalls overlap
+// one another at the start), otherwise all tiles go in row-major order (edge
+// tiles then share L2-resident lines with their interior neighbours instead
+// of reading them from DRAM a second time).  While a CTA works on a tile it already takes
 // the next index and stages that tile by TMA as soon as the current tile's
 // last staged read is done, so loads overlap the collision and stores; and
 // since tiles are handed out in order, the tiles in flight stay a compact
@@ -495,10 +498,17 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
   const TileSplit<Cf, BY> ts(a, a.tma && aligned);
   const int ntiles = ts.ntx * ts.nty;
   const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
+  const bool edge_first = ts.ne * 20 > ntiles;
   auto origin = [&](int t, int& x0, int& y0) {
     int tx, ty;
-    if (t < ts.ne) ts.edge(t, tx, ty);
-    else ts.interior(t - ts.ne, tx, ty);
+    if (!edge_first) {
+      ty = t / ts.ntx;
+      tx = t - ty * ts.ntx;
+    } else if (t < ts.ne) {
+      ts.edge(t, tx, ty);
+    } else {
+      ts.interior(t - ts.ne, tx, ty);
+    }
     x0 = tx * 32;
     y0 = ty * BY;
   };
