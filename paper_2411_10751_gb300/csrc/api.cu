@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "hlbm.h"
@@ -59,7 +60,7 @@ struct hlbm_ctx {
     int buf, wb, hb;
     CUtensorMap map;
   };
-  std::vector<TMap> tmaps;
+  std::deque<TMap> tmaps;         // deque: pointers to entries stay valid as maps are added
   int* status = nullptr;          // device status word (bounded waits)
   unsigned long long* tile_ctr = nullptr;  // persistent step's tile counter
   bool ctr_reset = true;          // the counter must be zeroed before the next step
