@@ -495,7 +495,8 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _ncu_traffic(khash, args.storage, sched),
                          "algorithmic_bytes_per_node": bytes_per_node,
-                         "kernel": ("step3d_kernel" if case.lattice == "D3Q39" else
+                         "kernel": (("step3d_rows_kernel" if sched[2] == 2 and case.nx in (32, 64, 128, 256)
+                                     else "step3d_kernel") if case.lattice == "D3Q39" else
                                     ("step2d_persistent_kernel" if sched[2] == 2 else "step2d_kernel")) +
                                    f" ({sched[0]} rows, {sched[1]} nodes per thread)"},
             "e2e": e2e,

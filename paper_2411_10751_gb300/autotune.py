@@ -18,7 +18,7 @@ from .solver import HLBM
 CACHE = Path(__file__).resolve().parent / "_build" / "autotune.json"
 
 CANDIDATES_2D = [(8, 2, 1), (8, 1, 1), (16, 2, 1), (16, 1, 1), (4, 1, 1), (8, 2, 2), (8, 1, 2)]
-CANDIDATES_3D = [(8, 2, 1), (8, 1, 1), (4, 1, 1)]
+CANDIDATES_3D = [(8, 2, 2), (8, 2, 1), (8, 1, 1), (4, 1, 1)]
 
 
 def _key(lattice, nx, ny, nz, params, storage) -> str:

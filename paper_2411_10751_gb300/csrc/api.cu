@@ -247,8 +247,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor map of population buffer `buf` viewed as [Q][ny][nx] with a
-// wb x hb x 1 box; null if it cannot be encoded (the kernel then stages
-// every tile with plain loads).
+// wb x hb x 1 box (D2Q37), or as [Q][nz][ny][nx] with a wb x hb x 1 x 1 box
+// (D3Q39); null if it cannot be encoded (the kernels then stage every tile
+// with plain loads).
 const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
   for (auto& t : c->tmaps)
     if (t.buf == buf && t.wb == wb && t.hb == hb) return &t.map;
@@ -261,19 +262,39 @@ const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
   const CUtensorMapDataType dt = c->storage == ST_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : c->storage == ST_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->Q};
-  const cuuint64_t strides[2] = {(cuuint64_t)c->nx * c->elem, (cuuint64_t)c->N * c->elem};
-  const cuuint32_t box[3] = {(cuuint32_t)wb, (cuuint32_t)hb, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&t.map, dt, 3, c->pop[buf], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const bool d3 = c->lattice == HLBM_D3Q39;
+  const cuuint64_t e = (cuuint64_t)c->elem;
+  const cuuint64_t dims2[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->Q};
+  const cuuint64_t strides2[2] = {(cuuint64_t)c->nx * e, (cuuint64_t)c->N * e};
+  const cuuint64_t dims3[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)c->Q};
+  const cuuint64_t strides3[3] = {(cuuint64_t)c->nx * e, (cuuint64_t)c->nx * c->ny * e, (cuuint64_t)c->N * e};
+  const cuuint32_t box[4] = {(cuuint32_t)wb, (cuuint32_t)hb, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&t.map, dt, d3 ? 4 : 3, c->pop[buf], d3 ? dims3 : dims2, d3 ? strides3 : strides2, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return nullptr;
   c->tmaps.push_back(t);
   return &c->tmaps.back().map;
 }
 
 cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
-  if (c->lattice != 0) return launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->npt, c->stream);
+  if (c->lattice != 0) {
+    // persistent whole-row kernel: box of 256 / nx rows, and single rows
+    CUtensorMap maps3[2];
+    const CUtensorMap* tm = nullptr;
+    if (!moments && a.persistent && a.tma && (c->nx == 32 || c->nx == 64 || c->nx == 128 || c->nx == 256)) {
+      const int buf = (a.fin == c->pop[0]) ? 0 : 1;
+      const CUtensorMap* mb = tensor_map(c, buf, c->nx, 256 / c->nx);
+      const CUtensorMap* mr = tensor_map(c, buf, c->nx, 1);
+      if (mb && mr) {
+        maps3[0] = *mb;
+        maps3[1] = *mr;
+        tm = maps3;
+      }
+    }
+    return launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->npt, tm, c->stream);
+  }
   CUtensorMap maps[2];
   std::memset(maps, 0, sizeof(maps));
   a.tma_store = 0;
@@ -381,7 +402,7 @@ hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat, con
   c->rows = 8;
   // TMA needs a row pitch that is a multiple of 16 bytes
   const char* no_tma = std::getenv("HLBM_NO_TMA");
-  c->tma_ok = lattice == HLBM_D2Q37 && ((size_t)nx * c->elem) % 16 == 0 && !(no_tma && no_tma[0] == '1');
+  c->tma_ok = ((size_t)nx * c->elem) % 16 == 0 && !(no_tma && no_tma[0] == '1');
   const char* no_tma_st = std::getenv("HLBM_NO_TMA_STORE");
   c->tma_store_ok = c->tma_ok && !(no_tma_st && no_tma_st[0] == '1');
   const char* skip = std::getenv("HLBM_TEST_SKIP_TMA");

@@ -66,8 +66,10 @@ struct InitArgs {
 // npt: nodes per thread (1, or 2 on float2 lanes; 8- and 16-row tiles).
 cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool moments, int rows, int npt,
                               const CUtensorMap* tmap, cudaStream_t s);
+// tmap: {whole-row box, single-row} maps of the input buffer for the persistent
+// whole-row kernel (nx = 32, 64, 128, 256), or null.
 cudaError_t launch_step_d3q39(const StepArgs& a, int kind, int storage, bool moments, int rows, int npt,
-                              cudaStream_t s);
+                              const CUtensorMap* tmap, cudaStream_t s);
 // Sets the dynamic shared-memory limit of every D2Q37 kernel of a storage type
 // (call before the first launch, outside stream capture).
 cudaError_t configure_step_d2q37(int storage);

@@ -14,9 +14,9 @@ cudaError_t configure_step2d_bf16();
 void box_step2d_f32(int, bool, int, int*, int*, int*);
 void box_step2d_f16(int, bool, int, int*, int*, int*);
 void box_step2d_bf16(int, bool, int, int*, int*, int*);
-cudaError_t launch_step3d_f32(const StepArgs&, int, bool, int, int, cudaStream_t);
-cudaError_t launch_step3d_f16(const StepArgs&, int, bool, int, int, cudaStream_t);
-cudaError_t launch_step3d_bf16(const StepArgs&, int, bool, int, int, cudaStream_t);
+cudaError_t launch_step3d_f32(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
+cudaError_t launch_step3d_f16(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
+cudaError_t launch_step3d_bf16(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
 
 cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool mom, int rows, int npt,
                               const CUtensorMap* tm, cudaStream_t s) {
@@ -48,11 +48,11 @@ void step_box_d2q37(int kind, int storage, bool mom, int rows, int* wb, int* hb,
 }
 
 cudaError_t launch_step_d3q39(const StepArgs& a, int kind, int storage, bool mom, int rows, int npt,
-                              cudaStream_t s) {
+                              const CUtensorMap* tm, cudaStream_t s) {
   switch (storage) {
-    case ST_F32: return launch_step3d_f32(a, kind, mom, rows, npt, s);
-    case ST_F16: return launch_step3d_f16(a, kind, mom, rows, npt, s);
-    case ST_BF16: return launch_step3d_bf16(a, kind, mom, rows, npt, s);
+    case ST_F32: return launch_step3d_f32(a, kind, mom, rows, npt, tm, s);
+    case ST_F16: return launch_step3d_f16(a, kind, mom, rows, npt, tm, s);
+    case ST_BF16: return launch_step3d_bf16(a, kind, mom, rows, npt, tm, s);
   }
   return cudaErrorInvalidValue;
 }

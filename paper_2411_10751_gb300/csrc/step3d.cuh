@@ -8,6 +8,7 @@
 #pragma once
 
 #include "step_common.cuh"
+#include "tma.cuh"
 
 namespace hlbm {
 
@@ -135,10 +136,205 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas3<MOM, NPT>()))
   }
 }
 
-// rows: 4 or 8 tile rows; npt: nodes per thread (2 needs 8 rows).
+// Persistent D3Q39 step on tiles of 256 nodes that span whole x-rows
+// (nx = 32, 64, 128 or 256; a tile is 256 / nx rows of one z-plane).  Each
+// population plane of a tile is one 4D tensor box at x = 0 shifted by
+// (-c_y, -c_z), so the periodic wrap in x is an index mask in shared memory
+// and the wrap in z a wrapped box coordinate; a plane whose rows cross the
+// domain's y-edge is copied row by row with wrapped y.  Tiles come in order
+// (y rows, then z planes) from the step's device counter; as soon as a tile's
+// populations are in registers the CTA takes the next index and issues its
+// copies, so the loads overlap the collision and the stores.  Two nodes per
+// thread (tile nodes t and t + 128) on the paired FP32 lanes.
+constexpr int kRows3Nodes = 256;
+
 template <int ST>
-cudaError_t launch_step3d_st(const StepArgs& a, int kind, bool mom, int rows, int npt, cudaStream_t s) {
+constexpr int rows3_smem() {
+  return D3Q39::Q * kRows3Nodes * (int)sizeof(typename Codec<ST>::T) + 16;
+}
+
+// c_y, c_z of D3Q39 velocity p for a runtime p (a fold over the compile-time
+// table; each issuing thread does one lookup).
+template <int... I>
+__device__ __forceinline__ void d3_cyz(int p, int& cy, int& cz, iseq<I...>) {
+  ((cy = (p == I) ? D3Q39::c(I, 1) : cy), ...);
+  ((cz = (p == I) ? D3Q39::c(I, 2) : cz), ...);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(128, 3)
+    step3d_rows_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tm_box,
+                       const __grid_constant__ CUtensorMap tm_row) {
+  using L = D3Q39;
+  using C = Codec<ST>;
+  using T = typename C::T;
+  using V = float2;
+  constexpr int NT = 128, TN = kRows3Nodes;
+  constexpr uint32_t TX = (uint32_t)(L::Q * TN * (int)sizeof(T));
+  constexpr float Dc = (float)(3.0 * L::cs2);
+  constexpr float inv_c0 = (float)(1.0 / L::c0);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_next[2];
+  T* sp = reinterpret_cast<T*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::Q * TN * (int)sizeof(T));
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int by = TN / nx;
+  const int nty = (ny + by - 1) / by;
+  const int ntiles = nty * nz;
+  const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
+  const int tid = threadIdx.x, xm = nx - 1;
+  int xk[2], rk[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int j = tid + NT * k;
+    xk[k] = j & xm;
+    rk[k] = j / nx;
+  }
+  int pcy = 0, pcz = 0;   // this thread's plane (tid < Q) for issuing copies
+  if (tid < L::Q) d3_cyz(tid, pcy, pcz, typename make_iseq<L::Q>::type{});
+  // threads tid < Q: the copies of plane tid of tile t (the barrier is armed)
+  auto issue_plane = [&](int t) {
+    const int z = t / nty, y0 = (t - z * nty) * by;
+    const int zz = wrap_near3(z - pcz, nz);
+    const int ys = y0 - pcy;
+    fence_proxy_async_smem();
+    if (ys >= 0 && ys + by <= ny) {
+      tma_load_4d(sp + tid * TN, &tm_box, 0, ys, zz, tid, bar);
+    } else {
+      for (int r = 0; r < by; ++r) {
+        const int yy = ((ys + r) % ny + ny) % ny;   // rows may pass several periods when ny < by + 6
+        tma_load_4d(sp + tid * TN + r * nx, &tm_row, 0, yy, zz, tid, bar);
+      }
+    }
+  };
+  // tid 0: takes the next tile index into slot `slot` and arms the barrier for it
+  auto take = [&](int slot) {
+    const int t = (int)(atomicAdd(a.tile_ctr, 1ull) % period);
+    s_next[slot] = t;
+    if (t < ntiles) mbar_arrive_expect_tx(bar, TX);
+  };
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    take(0);
+  }
+  __syncthreads();
+  int t = s_next[0];
+  if (t < ntiles && tid < L::Q && !a.debug_skip_tma) issue_plane(t);
+  uint32_t phase = 0;
+  for (int it = 1; t < ntiles; ++it) {
+    const int z = t / nty, y0 = (t - z * nty) * by;
+    const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
+      mbar_wait_bounded(bar, phase, a.wait_ns);
+      __syncthreads();
+      return;
+    }
+    phase ^= 1u;
+    if (tid == 0) take(it & 1);   // the barrier's next phase belongs to the next tile
+    V g[L::Q];
+    static_for<L::Q>([&](auto I) {
+      constexpr int i = I;
+      constexpr int cx = L::c(i, 0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) set_lane(g[i], k, to_float(sp[i * TN + rk[k] * nx + ((xk[k] - cx) & xm)]));
+    });
+    __syncthreads();  // the staging buffer is free and the next index is published
+    const int tn = s_next[it & 1];
+    if (tn < ntiles && tid < L::Q && !a.debug_skip_tma) issue_plane(tn);
+
+    int yk[2], nodek[2];
+    bool activek[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int y = y0 + rk[k];
+      activek[k] = y < ny;
+      yk[k] = y < ny ? y : y - ny;
+      nodek[k] = (z * ny + yk[k]) * nx + xk[k];
+    }
+    V dr, acc, J[3], Pih;
+    moments_h<L>(g, dr, acc, J, Pih);
+    const V rho = vadd(splat<V>(a.rho0), dr);
+    V ga[3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      float gk[3];
+      accel<3>(a, nodek[k], yk[k], gk);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) set_lane(ga[d], k, gk[d]);
+    }
+    const V F0 = vmul(rho, ga[0]), F1 = vmul(rho, ga[1]), F2 = vmul(rho, ga[2]);
+    const V inv_rho = vmap(rho, [](float r) { return 1.f / r; });
+    const V ux = vmul(vfma(splat<V>(0.5f), F0, J[0]), inv_rho);
+    const V uy = vmul(vfma(splat<V>(0.5f), F1, J[1]), inv_rho);
+    const V uz = vmul(vfma(splat<V>(0.5f), F2, J[2]), inv_rho);
+    const V uu = vfma(ux, ux, vfma(uy, uy, vmul(uz, uz)));
+    const V G2 = vmul(splat<V>(2.f), vfma(ux, F0, vfma(uy, F1, vmul(uz, F2))));
+    const V tb_m =
+        vmul(vmul(vfma(splat<V>(0.5f), G2, vsub(Pih, vmul(rho, uu))), inv_rho), splat<V>(1.f / Dc));
+    NodeSrcT<V> s;
+    s.dr = splat<V>(0.f);  // density deviation re-enters in apply_poly_h
+    s.rho = rho;
+    s.tb = a.isothermal ? splat<V>(0.f) : tb_m;
+    s.u[0] = vmul(ux, splat<V>(inv_c0));
+    s.u[1] = vmul(uy, splat<V>(inv_c0));
+    s.u[2] = vmul(uz, splat<V>(inv_c0));
+    s.F[0] = vmul(F0, splat<V>(inv_c0));
+    s.F[1] = vmul(F1, splat<V>(inv_c0));
+    s.F[2] = vmul(F2, splat<V>(inv_c0));
+    s.hG[0] = s.hG[1] = s.hG[2] = splat<V>(0.f);
+    s.sigma = splat<V>(0.f);
+    V K[20];
+    poly3<L>(s, a.omega, a.beta, K);
+    const float om1 = 1.f - a.omega;
+    K[0] = vfma(splat<V>(-om1), acc, K[0]);
+    apply_poly_h<L, 20>(g, K, om1, dr);
+    T* __restrict__ fout = static_cast<T*>(a.fout);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!activek[k]) continue;
+      static_for<L::Q>([&](auto I) {
+        constexpr int i = I;
+        C::st(fout + (size_t)i * (size_t)a.N + nodek[k], lane(g[i], k));
+      });
+    }
+    t = tn;
+  }
+}
+
+// Whether the whole-row persistent kernel serves this domain.
+inline bool rows3_eligible(const StepArgs& a) {
+  return a.tma && (a.nx == 32 || a.nx == 64 || a.nx == 128 || a.nx == 256);
+}
+
+template <int ST>
+int rows3_ctas() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step3d_rows_kernel<ST>, 128, rows3_smem<ST>());
+    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return n;
+}
+
+// rows: 4 or 8 tile rows; npt: nodes per thread (2 needs 8 rows); tmaps: the
+// whole-row box and single-row maps of the input buffer (persistent kernel),
+// or null.
+template <int ST>
+cudaError_t launch_step3d_st(const StepArgs& a, int kind, bool mom, int rows, int npt, const CUtensorMap* tmaps,
+                             cudaStream_t s) {
   if (kind != KIND_LOCAL) return cudaErrorInvalidValue;
+  if (!mom && a.persistent && tmaps && rows3_eligible(a)) {
+    const int by = kRows3Nodes / a.nx;
+    const int tiles = ((a.ny + by - 1) / by) * a.nz;
+    const int ctas = std::min(tiles, rows3_ctas<ST>());
+    step3d_rows_kernel<ST><<<ctas, 128, rows3_smem<ST>(), s>>>(a, tmaps[0], tmaps[1]);
+    return cudaGetLastError();
+  }
   const int by = (rows == 4) ? 4 : 8;
   const dim3 grid((a.nx + 31) / 32, (a.ny + by - 1) / by, a.nz);
   if (mom) step3d_kernel<ST, true, 8, 1><<<dim3((a.nx + 31) / 32, (a.ny + 7) / 8, a.nz), dim3(32, 8), 0, s>>>(a);

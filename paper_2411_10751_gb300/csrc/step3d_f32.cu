@@ -2,7 +2,8 @@
 #include "step3d.cuh"
 
 namespace hlbm {
-cudaError_t launch_step3d_f32(const StepArgs& a, int kind, bool mom, int rows, int npt, cudaStream_t s) {
-  return launch_step3d_st<ST_F32>(a, kind, mom, rows, npt, s);
+cudaError_t launch_step3d_f32(const StepArgs& a, int kind, bool mom, int rows, int npt, const CUtensorMap* tm,
+                              cudaStream_t s) {
+  return launch_step3d_st<ST_F32>(a, kind, mom, rows, npt, tm, s);
 }
 }  // namespace hlbm

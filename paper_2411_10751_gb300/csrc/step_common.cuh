@@ -133,6 +133,8 @@ __host__ __device__ constexpr int mono3_index(int p, int q, int r) {
 }
 
 // ------------------------------------------------------------- index wrap
+// v mod n for v in [-n, 2n) (no integer division)
+__device__ __forceinline__ int wrap_near3(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 __device__ __forceinline__ int wrap1(int v, int n) {  // v in [-n, 2n)
   v += (v < 0) ? n : 0;
   v -= (v >= n) ? n : 0;

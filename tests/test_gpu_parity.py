@@ -150,18 +150,20 @@ def test_d3q39_taylor_green_parity(HLBM):
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
-@pytest.mark.parametrize("rows,npt", [(4, 1), (8, 1), (8, 2)])
-def test_d3q39_schedules(HLBM, rows, npt):
-    """Every D3Q39 tile shape (one node per thread, or two on paired lanes) on a
-    ragged box with a full acceleration field."""
-    c = W.taylor_green_3d(n=24, tau_hat=0.7, Ma=0.2)
-    sl = (slice(0, 13), slice(0, 19), slice(0, 22))
+@pytest.mark.parametrize("rows,npt,pers,nx", [(4, 1, 1, 22), (8, 1, 1, 22), (8, 2, 1, 22), (8, 2, 2, 22),
+                                               (8, 2, 2, 32), (8, 2, 2, 64)])
+def test_d3q39_schedules(HLBM, rows, npt, pers, nx):
+    """Every D3Q39 tile shape (one node per thread, two on paired lanes, and the
+    persistent whole-row kernel, which serves nx = 32 and 64 here and falls back
+    to the grid kernel at nx = 22) on a ragged box with a full acceleration field."""
+    c = W.taylor_green_3d(n=64, tau_hat=0.7, Ma=0.2)
+    sl = (slice(0, 13), slice(0, 19), slice(0, nx))
     c.rho, c.theta = c.rho[sl].copy(), c.theta[sl].copy()
     c.u = c.u[(slice(None),) + sl].copy()
     c.nz, c.ny, c.nx = c.rho.shape
     rng = np.random.default_rng(3)
     c.gfield = W.fp32(2e-5 * (2 * rng.random((3,) + c.rho.shape) - 1))
-    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt)
+    mg, mo = run_pair(HLBM, c, 30, rows=rows, npt=npt, persistent=pers)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
