@@ -142,6 +142,15 @@ def test_droplet_512_full_size(HLBM):
     assert er < TOL32 and et < TOL32 and eu < TOL32, (er, eu, et)
 
 
+@pytest.mark.parametrize("Tr", [0.7, 0.9])
+def test_carnahan_starling_droplet_parity(HLBM, Tr):
+    """Carnahan-Starling droplet as printed for Sec. 5.4 (a = 0.25, b = 4,
+    k = 3.02; 200 x 200, r0 = 50)."""
+    c = W.droplet(n=200, r0=50.0, Tr=Tr, k=3.02, eos="cs")
+    mg, mo = run_pair(HLBM, c, 100)
+    assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
+
+
 def test_d3q39_taylor_green_parity(HLBM):
     c = W.taylor_green_3d(n=16, tau_hat=0.6, Ma=0.3)
     rng = np.random.default_rng(0)

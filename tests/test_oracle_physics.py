@@ -171,10 +171,14 @@ def test_tabulated_coexistence_densities():
     for Tr, (rg, rl) in W.VDW_COEXIST.items():
         g, l, _ = eos.maxwell("vdw", W.VDW_A, W.VDW_B, Tr * W.VDW_TC)
         assert abs(g - rg) < 1e-9 and abs(l - rl) < 1e-9
+    assert abs(eos.critical_temperature("cs", W.CS_A, W.CS_B) - W.CS_TC) < 1e-12
+    for Tr, (rg, rl) in W.CS_COEXIST.items():
+        g, l, _ = eos.maxwell("cs", W.CS_A, W.CS_B, Tr * W.CS_TC)
+        assert abs(g - rg) < 1e-10 and abs(l - rl) < 1e-10
 
 
-def _flat_interface(k, steps=10000):
-    c = W.flat_interface(nx=8, ny=200, tau_hat=0.8, Tr=0.85, k=k)
+def _flat_interface(k, steps=10000, Tr=0.85, kind="vdw"):
+    c = W.flat_interface(nx=8, ny=200, tau_hat=0.8, Tr=Tr, k=k, eos=kind)
     o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
     o.init(c.rho, c.u, c.theta)
     o.run(steps)
@@ -197,3 +201,19 @@ def test_flat_interface_tuned_k_matches_maxwell():
     pg = eos.pressure("vdw", rg, p["eos_a"], p["eos_b"], p["eos_T"])
     pl = eos.pressure("vdw", rl, p["eos_a"], p["eos_b"], p["eos_T"])
     assert abs(pg - pl) < 2e-2 * pl
+
+
+@pytest.mark.parametrize("Tr", [0.7, 0.8, 0.9])
+def test_flat_interface_carnahan_starling_paper_k_matches_maxwell(Tr):
+    """Sec. 5.4 prints k = 3.02 for the Carnahan-Starling EOS (a = 0.25, b = 4)
+    as the value that brings the coexistence curve onto Maxwell's: with the
+    reading tau = tau^ - 1/2 in P_i (Eq. 3.12) the flat interface's bulk
+    densities land within 1% of the equal-area densities."""
+    rg, rl, c = _flat_interface(3.02, 10000, Tr, "cs")
+    assert abs(rg / c.meta["rho_g"] - 1) < 1e-2, (rg, c.meta["rho_g"])
+    assert abs(rl / c.meta["rho_l"] - 1) < 1e-2, (rl, c.meta["rho_l"])
+
+
+def test_flat_interface_carnahan_starling_without_pressure_source_underestimates_gas():
+    rg, rl, c = _flat_interface(0.0, 10000, 0.9, "cs")
+    assert rg < 0.9 * c.meta["rho_g"]

@@ -60,6 +60,21 @@ VDW_COEXIST = {
     0.95: (2.026552243876127, 5.116045703149),
 }
 
+# Carnahan-Starling EOS as printed for Sec. 5.4 (Eq. 5.9): a = 0.25, b = 4;
+# T_c and the coexistence densities from the oracle's Maxwell solver (checked
+# against it by the tests).
+CS_A = 0.25
+CS_B = 4.0
+CS_TC = 0.023582175788041854
+CS_COEXIST = {
+    0.70: (0.009294146227023828, 0.3581309411215158),
+    0.75: (0.014526084623691983, 0.3332415984642653),
+    0.80: (0.021723243437775562, 0.3071956822831783),
+    0.85: (0.03158177953528134, 0.2792620941620207),
+    0.90: (0.04542119811463903, 0.24808424109070054),
+    0.95: (0.06661162931376641, 0.21025422466496013),
+}
+
 # D3Q39 lattice constant squared (the degree-7 lattice has c0^2 = 2/3); only
 # used here to express the Taylor-Green pressure field and Mach number in
 # lattice units.
@@ -142,40 +157,49 @@ def thermal_decay(n: int = 1024, tau_hat: float = 0.7, Pr: float = 0.71, seed: i
                 meta=dict(seed=seed, eps_T=eps_T, u0=u0))
 
 
-def _multiphase_params(Tr: float, k: float, rho_g: float, rho_l: float) -> dict:
-    return source_params(SC=True, P=True, isothermal=True, eos="vdw", eos_a=VDW_A, eos_b=VDW_B,
-                         eos_T=Tr * VDW_TC, k=k, rho0=0.5 * (rho_g + rho_l))
+def _multiphase_params(Tr: float, k: float, rho_g: float, rho_l: float, eos: str = "vdw") -> dict:
+    # Stored populations are deviations from rho0.  u = j / rho divides their
+    # absolute rounding error by the density, so the gas (the smaller density)
+    # is the reference: its populations are stored as the smallest numbers.
+    a, b, tc = (VDW_A, VDW_B, VDW_TC) if eos == "vdw" else (CS_A, CS_B, CS_TC)
+    return source_params(SC=True, P=True, isothermal=True, eos=eos, eos_a=a, eos_b=b,
+                         eos_T=Tr * tc, k=k, rho0=rho_g)
+
+
+def _coexistence(eos: str, Tr: float):
+    return (VDW_COEXIST if eos == "vdw" else CS_COEXIST)[round(Tr, 2)]
 
 
 def droplet(n: int = 512, tau_hat: float = 0.8, Tr: float = 0.85, k: float = 0.01,
             r0: float | None = None, W: float = 5.0, steps: int = 20000,
-            nx: int | None = None, ny: int | None = None) -> Case:
+            nx: int | None = None, ny: int | None = None, eos: str = "vdw") -> Case:
     """Liquid disk (Eq. 5.11, droplet branch) of radius r0 centred at (nx/2, ny/2),
-    tanh interface of width W, coexistence densities from Maxwell's rule."""
+    tanh interface of width W, coexistence densities from Maxwell's rule;
+    van der Waals (eos="vdw") or Carnahan-Starling (eos="cs", Eq. 5.9)."""
     nx = nx or n
     ny = ny or n
     r0 = 100.0 if r0 is None else r0
-    rho_g, rho_l = VDW_COEXIST[round(Tr, 2)]
+    rho_g, rho_l = _coexistence(eos, Tr)
     x = np.arange(nx, dtype=np.float64)[None, :]
     y = np.arange(ny, dtype=np.float64)[:, None]
     d = np.sqrt((x - nx / 2.0) ** 2 + (y - ny / 2.0) ** 2)
     rho = 0.5 * (rho_l + rho_g) - 0.5 * (rho_l - rho_g) * np.tanh(2.0 * (d - r0) / W)
-    return Case("droplet", "D2Q37", nx, ny, 1, tau_hat, _multiphase_params(Tr, k, rho_g, rho_l),
+    return Case("droplet", "D2Q37", nx, ny, 1, tau_hat, _multiphase_params(Tr, k, rho_g, rho_l, eos),
                 rho, np.zeros((2, ny, nx)), np.ones((ny, nx)), None, steps,
-                meta=dict(Tr=Tr, rho_g=rho_g, rho_l=rho_l, r0=r0, W=W))
+                meta=dict(Tr=Tr, rho_g=rho_g, rho_l=rho_l, r0=r0, W=W, eos=eos))
 
 
 def flat_interface(nx: int = 8, ny: int = 200, tau_hat: float = 0.8, Tr: float = 0.85,
-                   k: float = 0.01, W: float = 5.0) -> Case:
+                   k: float = 0.01, W: float = 5.0, eos: str = "vdw") -> Case:
     """Liquid slab between y = ny/4 and 3 ny/4 (Eq. 5.10 with the 50 x 200 geometry of Sec. 5.4)."""
-    rho_g, rho_l = VDW_COEXIST[round(Tr, 2)]
+    rho_g, rho_l = _coexistence(eos, Tr)
     y = np.arange(ny, dtype=np.float64)
     prof = rho_g + 0.5 * (rho_l - rho_g) * np.abs(np.tanh(2.0 * (y - ny / 4.0) / W)
                                                   - np.tanh(2.0 * (y - 3.0 * ny / 4.0) / W))
     rho = np.broadcast_to(prof[:, None], (ny, nx)).copy()
-    return Case("flat_interface", "D2Q37", nx, ny, 1, tau_hat, _multiphase_params(Tr, k, rho_g, rho_l),
+    return Case("flat_interface", "D2Q37", nx, ny, 1, tau_hat, _multiphase_params(Tr, k, rho_g, rho_l, eos),
                 rho, np.zeros((2, ny, nx)), np.ones((ny, nx)), None, 5000,
-                meta=dict(Tr=Tr, rho_g=rho_g, rho_l=rho_l))
+                meta=dict(Tr=Tr, rho_g=rho_g, rho_l=rho_l, eos=eos))
 
 
 def shear_wave(nx: int = 8, ny: int = 128, tau_hat: float = 0.8, u0: float = 1e-3) -> Case:
