@@ -80,11 +80,15 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# the sources that define the 2D fused step kernels (what the DRAM counters describe)
+STEP2D_SOURCES = ("step2d.cuh", "step_common.cuh", "tma.cuh", "lattice.cuh", "lattice_gen.cpp", "internal.h",
+                  "step2d_f32.cu", "step2d_f16.cu", "step2d_bf16.cu")
+
+
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_2411_10751_gb300" / "csrc").glob("*")):
-        if f.suffix in (".cu", ".cuh", ".h", ".cpp"):
-            h.update(f.read_bytes())
+    for name in STEP2D_SOURCES:
+        h.update((ROOT / "paper_2411_10751_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -99,10 +103,12 @@ def _ncu_traffic(kernel_hash: str, storage: str, schedule):
         d = json.loads(p.read_text())
     except ValueError:
         return None
-    e = d.get(storage)
-    if not e or d.get("kernel_source_sha") != kernel_hash or list(e.get("schedule", [])) != list(schedule):
+    if d.get("kernel_source_sha") != kernel_hash:
         return None
-    return e.get("dram_bytes_per_launch")
+    for e in d.get("entries", []):
+        if e.get("storage") == storage and list(e.get("schedule", [])) == list(schedule):
+            return e.get("dram_bytes_per_launch")
+    return None
 
 
 class ClockSampler:
