@@ -1,9 +1,11 @@
 // Batched step: many independent periodic D2Q37 domains (any sizes, sources
-// and parameters) advanced by one launch per time step, replayed from a CUDA
-// graph.  Each CTA takes one 32 x 8 tile of one domain from a tile -> domain
-// work list; the domain's step arguments (for both buffer parities) and its
-// TMA tensor maps are read from device memory, so the tile work is exactly
-// the single-domain kernel's (process_tile).
+// and parameters) advanced by one launch per source kind and time step,
+// replayed from a CUDA graph.  Each CTA takes one 32 x 8 tile of one domain
+// from a tile -> domain work list (grouped by kind, so each kind's kernel gets
+// its own shared-memory size and register budget); the domain's step
+// arguments (for both buffer parities) and its TMA tensor maps are read from
+// device memory, so the tile work is exactly the single-domain kernel's
+// (process_tile).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -30,14 +32,6 @@ struct alignas(64) BatchDomain {
   int cur;                // buffer holding the state at the start of the batch call
   int has_map;
 };
-
-template <int ST>
-constexpr int batch_smem() {
-  constexpr int a = Cfg2<ST, KIND_LOCAL, false, kRows>::SMEM;
-  constexpr int b = Cfg2<ST, KIND_THERMAL, false, kRows>::SMEM;
-  constexpr int c = Cfg2<ST, KIND_SC, false, kRows>::SMEM;
-  return std::max(a, std::max(b, c));
-}
 
 template <int ST, int KIND>
 __device__ __forceinline__ void batch_tile(const BatchDomain& dom, const StepArgs& a, unsigned char* smem, int x0,
@@ -68,33 +62,52 @@ __device__ __forceinline__ void batch_tile(const BatchDomain& dom, const StepArg
   process_tile<ST, KIND, false, kRows, kNpt, false>(a, nullptr, smem, x0, y0, [] {});
 }
 
-template <int ST>
-__global__ void __launch_bounds__(32 * kRows / kNpt, 2)
-    batch_step_kernel(const BatchDomain* __restrict__ doms, const int* __restrict__ item_dom, int flip) {
+// Tiles base .. base + gridDim.x - 1 of the work list, all of kind KIND.
+template <int ST, int KIND>
+__global__ void __launch_bounds__(32 * kRows / kNpt, (min_ctas2<ST, KIND, false, kRows, kNpt>()))
+    batch_step_kernel(const BatchDomain* __restrict__ doms, const int* __restrict__ item_dom, int base, int flip) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int d = item_dom[blockIdx.x];
+  const int gi = base + blockIdx.x;
+  const int d = item_dom[gi];
   const BatchDomain& dom = doms[d];
   const int par = dom.cur ^ flip;
   const StepArgs& a = dom.args[par];
-  const int t = blockIdx.x - dom.tile0;
+  const int t = gi - dom.tile0;
   const int ty = t / dom.tiles_x;
   const int x0 = (t - ty * dom.tiles_x) * 32, y0 = ty * kRows;
-  switch (dom.kind) {
-    case KIND_SC: batch_tile<ST, KIND_SC>(dom, a, smem, x0, y0, par); break;
-    case KIND_THERMAL: batch_tile<ST, KIND_THERMAL>(dom, a, smem, x0, y0, par); break;
-    default: batch_tile<ST, KIND_LOCAL>(dom, a, smem, x0, y0, par); break;
-  }
+  batch_tile<ST, KIND>(dom, a, smem, x0, y0, par);
 }
 
-template <int ST>
-cudaError_t launch_batch(const BatchDomain* doms, const int* items, int nitems, int flip, cudaStream_t s) {
-  batch_step_kernel<ST><<<nitems, dim3(32, kRows / kNpt, 1), batch_smem<ST>(), s>>>(doms, items, flip);
+template <int ST, int KIND>
+cudaError_t launch_batch_kind(const BatchDomain* doms, const int* items, int base, int count, int flip,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  batch_step_kernel<ST, KIND><<<count, dim3(32, kRows / kNpt, 1), Cfg2<ST, KIND, false, kRows>::SMEM, s>>>(
+      doms, items, base, flip);
   return cudaGetLastError();
+}
+
+// off[k], cnt[k]: the work-list segment of kind k (KIND_LOCAL, KIND_THERMAL, KIND_SC)
+template <int ST>
+cudaError_t launch_batch(const BatchDomain* doms, const int* items, const int* off, const int* cnt, int flip,
+                         cudaStream_t s) {
+  cudaError_t e = launch_batch_kind<ST, KIND_LOCAL>(doms, items, off[KIND_LOCAL], cnt[KIND_LOCAL], flip, s);
+  if (e == cudaSuccess) e = launch_batch_kind<ST, KIND_THERMAL>(doms, items, off[KIND_THERMAL], cnt[KIND_THERMAL], flip, s);
+  if (e == cudaSuccess) e = launch_batch_kind<ST, KIND_SC>(doms, items, off[KIND_SC], cnt[KIND_SC], flip, s);
+  return e;
 }
 
 template <int ST>
 cudaError_t configure_batch() {
-  return cudaFuncSetAttribute(batch_step_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<ST>());
+  cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<ST, KIND_LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg2<ST, KIND_LOCAL, false, kRows>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_step_kernel<ST, KIND_THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg2<ST, KIND_THERMAL, false, kRows>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_step_kernel<ST, KIND_SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg2<ST, KIND_SC, false, kRows>::SMEM);
+  return e;
 }
 
 template <int ST>
@@ -138,7 +151,8 @@ struct hlbm_batch {
   int storage = 0;
   cudaStream_t stream = nullptr;
   std::vector<BatchDomain> host;
-  std::vector<int> items;
+  std::vector<int> items;         // tile -> domain, grouped by kind
+  int off[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};   // each kind's segment of `items`
   BatchDevice dev;
   cudaGraphExec_t graph = nullptr;
   std::string msg;
@@ -197,33 +211,36 @@ hlbm_status hlbm_batch_create(int n, hlbm_ctx* const* ctxs, hlbm_batch** out) {
 static hlbm_status batch_refresh(hlbm_batch* b) {
   b->host.assign(b->ctxs.size(), BatchDomain{});
   b->items.clear();
-  int tile0 = 0;
-  for (size_t k = 0; k < b->ctxs.size(); ++k) {
-    hlbm_ctx* c = b->ctxs[k];
-    int st, kind, nx, ny;
-    ctx_batchable(c, &st, &kind, &nx, &ny);
-    BatchDomain& d = b->host[k];
-    std::memset(&d, 0, sizeof(d));
-    d.kind = kind;
-    d.tiles_x = (nx + 31) / 32;
-    d.tile0 = tile0;
-    d.cur = ctx_cur(c);
-    d.args[0] = ctx_step_args(c, 0);
-    d.args[1] = ctx_step_args(c, 1);
-    int wb = 0, hb = 0;
-    if (st == ST_F32) box_for_kind<ST_F32>(kind, wb, hb);
-    else if (st == ST_F16) box_for_kind<ST_F16>(kind, wb, hb);
-    else box_for_kind<ST_BF16>(kind, wb, hb);
-    const CUtensorMap* m0 = d.args[0].tma ? ctx_tensor_map(c, 0, wb, hb) : nullptr;
-    const CUtensorMap* m1 = d.args[0].tma ? ctx_tensor_map(c, 1, wb, hb) : nullptr;
-    d.has_map = (m0 && m1) ? 1 : 0;
-    if (d.has_map) {
-      d.tmap[0] = *m0;
-      d.tmap[1] = *m1;
+  for (int kind : {(int)KIND_LOCAL, (int)KIND_THERMAL, (int)KIND_SC}) {
+    b->off[kind] = (int)b->items.size();
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+      hlbm_ctx* c = b->ctxs[k];
+      int st, dkind, nx, ny;
+      ctx_batchable(c, &st, &dkind, &nx, &ny);
+      if (dkind != kind) continue;
+      BatchDomain& d = b->host[k];
+      std::memset(&d, 0, sizeof(d));
+      d.kind = dkind;
+      d.tiles_x = (nx + 31) / 32;
+      d.tile0 = (int)b->items.size();
+      d.cur = ctx_cur(c);
+      d.args[0] = ctx_step_args(c, 0);
+      d.args[1] = ctx_step_args(c, 1);
+      int wb = 0, hb = 0;
+      if (st == ST_F32) box_for_kind<ST_F32>(dkind, wb, hb);
+      else if (st == ST_F16) box_for_kind<ST_F16>(dkind, wb, hb);
+      else box_for_kind<ST_BF16>(dkind, wb, hb);
+      const CUtensorMap* m0 = d.args[0].tma ? ctx_tensor_map(c, 0, wb, hb) : nullptr;
+      const CUtensorMap* m1 = d.args[0].tma ? ctx_tensor_map(c, 1, wb, hb) : nullptr;
+      d.has_map = (m0 && m1) ? 1 : 0;
+      if (d.has_map) {
+        d.tmap[0] = *m0;
+        d.tmap[1] = *m1;
+      }
+      const int tiles = d.tiles_x * ((ny + kRows - 1) / kRows);
+      for (int t = 0; t < tiles; ++t) b->items.push_back((int)k);
     }
-    const int tiles = d.tiles_x * ((ny + kRows - 1) / kRows);
-    for (int t = 0; t < tiles; ++t) b->items.push_back((int)k);
-    tile0 += tiles;
+    b->cnt[kind] = (int)b->items.size() - b->off[kind];
   }
   cudaError_t e = batch_upload(b->host, b->items, b->dev, b->stream);
   if (e != cudaSuccess) {
@@ -235,9 +252,9 @@ static hlbm_status batch_refresh(hlbm_batch* b) {
 
 static cudaError_t batch_launch(hlbm_batch* b, int flip) {
   switch (b->storage) {
-    case ST_F32: return launch_batch<ST_F32>(b->dev.doms, b->dev.items, b->dev.nitems, flip, b->stream);
-    case ST_F16: return launch_batch<ST_F16>(b->dev.doms, b->dev.items, b->dev.nitems, flip, b->stream);
-    default: return launch_batch<ST_BF16>(b->dev.doms, b->dev.items, b->dev.nitems, flip, b->stream);
+    case ST_F32: return launch_batch<ST_F32>(b->dev.doms, b->dev.items, b->off, b->cnt, flip, b->stream);
+    case ST_F16: return launch_batch<ST_F16>(b->dev.doms, b->dev.items, b->off, b->cnt, flip, b->stream);
+    default: return launch_batch<ST_BF16>(b->dev.doms, b->dev.items, b->off, b->cnt, flip, b->stream);
   }
 }
 
