@@ -355,7 +355,9 @@ def adjoint_extra(lrank, n=128, steps=400, ckpt=50):
     import torch
     from paper_2411_10751_gb300.solver import HLBM
     c = W.taylor_green_3d(n=n, tau_hat=0.6, Ma=0.3, steps=steps)
+    sched = tuned_schedule(c, "f32", lrank)      # forward and recompute steps
     g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, device=lrank)
+    g.set_tile(*sched)
     g.set_force_field(c.gfield, "field")
     g.init(c.rho, c.u, c.theta)
     g.adjoint(4, 2)                      # warm-up of every kernel on the path
@@ -368,7 +370,7 @@ def adjoint_extra(lrank, n=128, steps=400, ckpt=50):
     g.close()
     return {"workload": f"D3Q39 Taylor-Green {n}^3, Ma 0.3, tau 0.6: dL/dg of the kinetic energy at step {steps}, "
                         f"checkpoint every {ckpt}",
-            "seconds": dt, "ms_per_reverse_step": dt * 1e3 / steps,
+            "seconds": dt, "ms_per_reverse_step": dt * 1e3 / steps, "forward_schedule": list(sched),
             "MLUPS_reverse": c.nodes * steps / dt / 1e6, "loss": loss,
             "note": "wall time of hlbm_adjoint_run: forward with checkpoints, segment recompute, reverse steps"}
 
@@ -413,6 +415,8 @@ def main():
                     help="forward workload of the line (default: the 1024^2 thermal-decay benchmark)")
     ap.add_argument("--only-device", action="store_true",
                     help="device-timed steps only (no e2e, variants, extras or CPU baseline; for profiling)")
+    ap.add_argument("--only-adjoint", action="store_true",
+                    help="run the adjoint extra alone and print its line (for profiling)")
     args = ap.parse_args()
     if args.only_device:
         args.no_variants = args.no_extras = args.no_cpu_baseline = True
@@ -432,6 +436,10 @@ def main():
         pkg.build()
     _barrier(ws)
     pkg.load()
+    if args.only_adjoint:
+        if rank == 0:
+            print(json.dumps({"adjoint": adjoint_extra(lrank)}))
+        return 0
 
     case = WORKLOADS[args.workload][0]()
     if args.schedule:

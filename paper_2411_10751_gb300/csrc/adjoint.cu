@@ -11,10 +11,10 @@
 // where Phi = sum_i mu_i (C_i - (1 - omega) f_i) = sum_ab B_ab M_ab / (a! b!)
 // (M the weighted Hermite moments of mu, B = omega a^eq + beta s the
 // coefficients of the collision), a polynomial in (rho, u, theta-bar, F).
-// Its partial derivatives come from a forward-mode dual-number evaluation;
-// the chain rule through u = j/rho + g/2, theta-bar(e, rho, u, g) and F = rho g
-// then gives the derivatives with respect to rho = sum f, j = sum c f,
-// e = sum |c|^2 f and g.
+// Its partial derivatives are contractions of M shifted by one or two indices
+// (phi_grad below); the chain rule through u = j/rho + g/2,
+// theta-bar(e, rho, u, g) and F = rho g then gives the derivatives with
+// respect to rho = sum f, j = sum c f, e = sum |c|^2 f and g.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -25,52 +25,6 @@
 
 namespace hlbm {
 namespace {
-
-// value and NV partial derivatives
-template <int NV>
-struct Dual {
-  float v;
-  float d[NV];
-};
-template <int NV>
-__device__ __forceinline__ Dual<NV> dconst(float c) {
-  Dual<NV> r;
-  r.v = c;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) r.d[k] = 0.f;
-  return r;
-}
-template <int NV>
-__device__ __forceinline__ Dual<NV> dvar(float v, int k0) {
-  Dual<NV> r = dconst<NV>(v);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) r.d[k] = (k == k0) ? 1.f : 0.f;
-  return r;
-}
-template <int NV>
-__device__ __forceinline__ Dual<NV> operator+(const Dual<NV>& a, const Dual<NV>& b) {
-  Dual<NV> r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-template <int NV>
-__device__ __forceinline__ Dual<NV> operator*(const Dual<NV>& a, const Dual<NV>& b) {
-  Dual<NV> r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) r.d[k] = fmaf(a.v, b.d[k], a.d[k] * b.v);
-  return r;
-}
-template <int NV>
-__device__ __forceinline__ Dual<NV> operator*(float s, const Dual<NV>& a) {
-  Dual<NV> r;
-  r.v = s * a.v;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) r.d[k] = s * a.d[k];
-  return r;
-}
 
 // He_n(c / c0) (n <= 4) at integer c, as a compile-time constant
 template <class L>
@@ -84,57 +38,116 @@ template <class L>
 struct AdjCfg {
   static constexpr int D = L::D;
   static constexpr int NM = (D == 2) ? 15 : 20;
-  static constexpr int NV = 2 * D + 2;  // rho, u (D), theta-bar, F (D)
   __host__ __device__ static constexpr int mono(int m, int ax) { return D == 2 ? (ax < 2 ? mono2(m, ax) : 0) : mono3(m, ax); }
+  __host__ __device__ static constexpr int index(int a, int b, int c) {
+    return D == 2 ? (c == 0 ? mono2_index(a, b) : -1) : mono3_index(a, b, c);
+  }
 };
 
-// Phi(rho, u, tb, F) = sum_m B_m M_m / (a! b! c!) with dual inputs in lattice units.
-template <class L>
-__device__ __forceinline__ Dual<AdjCfg<L>::NV> phi_dual(const float (&M)[AdjCfg<L>::NM], float rho, const float (&u)[3],
-                                                       float tb, const float (&F)[3], bool thermal, float omega,
-                                                       float beta) {
+// sum over the monomials (a, b, c) of order <= LIM of M[(a, b, c) + (SX, SY, SZ)] P_abc / (a! b! c!)
+template <class L, int SX, int SY, int SZ, int LIM>
+__device__ __forceinline__ float hshift(const float (&M)[AdjCfg<L>::NM], const float (&P)[AdjCfg<L>::NM]) {
   using A = AdjCfg<L>;
-  constexpr int D = A::D, NV = A::NV;
-  constexpr float inv_c0 = (float)(1.0 / L::c0);
-  const Dual<NV> r = dvar<NV>(rho, 0);
-  Dual<NV> ux[3], fx[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    ux[a] = (a < D) ? inv_c0 * dvar<NV>(u[a], 1 + a) : dconst<NV>(0.f);
-    fx[a] = (a < D) ? inv_c0 * dvar<NV>(F[a], 2 + D + a) : dconst<NV>(0.f);
-  }
-  const Dual<NV> t = thermal ? dvar<NV>(tb, 1 + D) : dconst<NV>(0.f);
-  // per-axis Gaussian Hermite moments m_0..m_4 of N(u, 1 + tb)
-  Dual<NV> m[3][5];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const Dual<NV> u2 = ux[a] * ux[a];
-    m[a][0] = dconst<NV>(1.f);
-    m[a][1] = ux[a];
-    m[a][2] = u2 + t;
-    m[a][3] = ux[a] * (u2 + 3.f * t);
-    m[a][4] = u2 * (u2 + 6.f * t) + 3.f * (t * t);
-  }
-  Dual<NV> phi = dconst<NV>(0.f);
+  float s = 0.f;
   static_for<A::NM>([&](auto Mi) {
     constexpr int mi = Mi;
     constexpr int a = A::mono(mi, 0), b = A::mono(mi, 1), c = A::mono(mi, 2);
-    constexpr int n = a + b + c;
-    // equilibrium coefficient (a_000 = rho)
-    Dual<NV> eq = r * (m[0][a] * (m[1][b] * m[2][c]));
-    Dual<NV> B = omega * eq;
-    if constexpr (n >= 1 && n <= 3) {
-      // body force: F . d/du of the equilibrium coefficient / rho
-      Dual<NV> src = dconst<NV>(0.f);
-      if constexpr (a > 0) src = src + ((float)a * fx[0]) * (m[0][a > 0 ? a - 1 : 0] * (m[1][b] * m[2][c]));
-      if constexpr (b > 0) src = src + ((float)b * fx[1]) * (m[0][a] * (m[1][b > 0 ? b - 1 : 0] * m[2][c]));
-      if constexpr (c > 0) src = src + ((float)c * fx[2]) * (m[0][a] * (m[1][b] * m[2][c > 0 ? c - 1 : 0]));
-      B = B + beta * src;
+    if constexpr (a + b + c <= LIM) {
+      constexpr int j = A::index(a + SX, b + SY, c + SZ);
+      static_assert(j >= 0, "shifted monomial outside the moment set");
+      constexpr float cf = (float)(1.0 / (fact_d(a) * fact_d(b) * fact_d(c)));
+      s = fmaf(M[j] * cf, P[mi], s);
     }
-    constexpr float inv_fact = (float)(1.0 / (fact_d(a) * fact_d(b) * fact_d(c)));
-    phi = phi + (inv_fact * M[mi]) * B;
   });
-  return phi;
+  return s;
+}
+
+// Partial derivatives of Phi(rho, u, tb, F) = sum_m B_m M_m / (a! b! c!) with
+// B_abc = omega rho P_abc + beta sum_d (F_d / c0) idx_d P_{abc - e_d} (the
+// body force for orders 1..3), P_abc = m_a(u_x/c0) m_b(u_y/c0) m_c(u_z/c0) and
+// m_k the Gaussian Hermite moments of N(u, 1 + tb).  Since dm_k/du~ = k m_{k-1}
+// and dm_k/dtb = k (k - 1) / 2 m_{k-2}, each derivative is the contraction of
+// M shifted by one or two indices with P:
+//   dPhi/drho = omega S,  S = sum_{n <= E} M_m P_m / m!          (E: equilibrium order)
+//   dPhi/dF_d = beta S_d / c0,  S_d = sum_{n <= 2} M_{m + e_d} P_m / m!
+//   dPhi/du_e = (omega rho sum_{n <= E-1} M_{m+e_e} P_m / m! + beta sum_d F~_d U_de) / c0,
+//               U_de = sum_{n <= 1} M_{m + e_d + e_e} P_m / m!
+//   dPhi/dtb  = omega rho / 2 sum_d sum_{n <= E-2} M_{m + 2 e_d} P_m / m!
+//               + beta / 2 sum_d F~_d sum_e M_{e_d + 2 e_e}
+template <class L>
+__device__ __forceinline__ void phi_grad(const float (&M)[AdjCfg<L>::NM], float rho, const float (&u)[3], float tb,
+                                         const float (&F)[3], bool thermal, float omega, float beta, float& Prho,
+                                         float (&Pu)[3], float& Pt, float (&PF)[3]) {
+  using A = AdjCfg<L>;
+  constexpr int D = A::D, NM = A::NM, E = L::FEQ_ORDER;
+  constexpr float inv_c0 = (float)(1.0 / L::c0);
+  const float t = thermal ? tb : 0.f;
+  float m[3][5];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float x = (a < D) ? u[a] * inv_c0 : 0.f;
+    const float x2 = x * x;
+    m[a][0] = 1.f;
+    m[a][1] = x;
+    m[a][2] = x2 + t;
+    m[a][3] = x * fmaf(3.f, t, x2);
+    m[a][4] = fmaf(x2, fmaf(6.f, t, x2), 3.f * t * t);
+  }
+  float P[NM];
+  static_for<NM>([&](auto Mi) {
+    constexpr int mi = Mi;
+    P[mi] = m[0][A::mono(mi, 0)] * (m[1][A::mono(mi, 1)] * m[2][A::mono(mi, 2)]);
+  });
+  const float Ft[3] = {F[0] * inv_c0, F[1] * inv_c0, D == 3 ? F[2] * inv_c0 : 0.f};
+  const float orho = omega * rho;
+  Prho = omega * hshift<L, 0, 0, 0, E>(M, P);
+  // first shifts: equilibrium (order E - 1) and body force (order 2)
+  float Eq[3] = {0.f, 0.f, 0.f}, Sd[3] = {0.f, 0.f, 0.f};
+  Eq[0] = hshift<L, 1, 0, 0, E - 1>(M, P);
+  Eq[1] = hshift<L, 0, 1, 0, E - 1>(M, P);
+  Sd[0] = (E - 1 == 2) ? Eq[0] : hshift<L, 1, 0, 0, 2>(M, P);
+  Sd[1] = (E - 1 == 2) ? Eq[1] : hshift<L, 0, 1, 0, 2>(M, P);
+  if constexpr (D == 3) {
+    Eq[2] = hshift<L, 0, 0, 1, E - 1>(M, P);
+    Sd[2] = (E - 1 == 2) ? Eq[2] : hshift<L, 0, 0, 1, 2>(M, P);
+  }
+  // second shifts of the body force (order 1), symmetric in (d, e)
+  float U[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  U[0][0] = hshift<L, 2, 0, 0, 1>(M, P);
+  U[1][1] = hshift<L, 0, 2, 0, 1>(M, P);
+  U[0][1] = U[1][0] = hshift<L, 1, 1, 0, 1>(M, P);
+  if constexpr (D == 3) {
+    U[2][2] = hshift<L, 0, 0, 2, 1>(M, P);
+    U[0][2] = U[2][0] = hshift<L, 1, 0, 1, 1>(M, P);
+    U[1][2] = U[2][1] = hshift<L, 0, 1, 1, 1>(M, P);
+  }
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    float s = orho * Eq[e];
+#pragma unroll
+    for (int d = 0; d < D; ++d) s = fmaf(beta * Ft[d], U[d][e], s);
+    Pu[e] = (e < D) ? s * inv_c0 : 0.f;
+    PF[e] = (e < D) ? beta * Sd[e] * inv_c0 : 0.f;
+  }
+  Pt = 0.f;
+  if (thermal) {
+    // equilibrium: second shifts in one axis (order E - 2)
+    float q = hshift<L, 2, 0, 0, E - 2>(M, P) + hshift<L, 0, 2, 0, E - 2>(M, P);
+    if constexpr (D == 3) q += hshift<L, 0, 0, 2, E - 2>(M, P);
+    // body force: sum_e M_{e_d + 2 e_e} (order 3, P_000 = 1)
+    float src = 0.f;
+    static_for<D>([&](auto Dd) {
+      constexpr int d = Dd;
+      float md = 0.f;
+      static_for<D>([&](auto Ee) {
+        constexpr int e = Ee;
+        constexpr int j = A::index((d == 0) + 2 * (e == 0), (d == 1) + 2 * (e == 1), (d == 2) + 2 * (e == 2));
+        md += M[j];
+      });
+      src = fmaf(Ft[d], md, src);
+    });
+    Pt = 0.5f * fmaf(orho, q, beta * src);
+  }
 }
 
 // Weighted Hermite moments M_m = sum_i w_i mu_i He_a(cx/c0) He_b(cy/c0) He_c(cz/c0).
@@ -252,7 +265,7 @@ template <class L, int ST>
 __global__ void __launch_bounds__(128) adjoint_step_kernel(const __grid_constant__ AdjArgs a) {
   using C = Codec<ST>;
   using A = AdjCfg<L>;
-  constexpr int D = L::D, NV = A::NV;
+  constexpr int D = L::D;
   constexpr float Dc = (float)(D * L::cs2);
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.N) return;
@@ -277,13 +290,10 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(const __grid_constant
   }
   float M[A::NM];
   hermite_moments<L>(mu, M);
-  const Dual<NV> phi = phi_dual<L>(M, q.rho, q.u, q.tb, q.F, a.thermal != 0, a.omega, a.beta);
-  const float Prho = phi.d[0], Pt = a.thermal ? phi.d[1 + D] : 0.f;
-  float qv[3], PF[3];
-  for (int d = 0; d < 3; ++d) {
-    PF[d] = (d < D) ? phi.d[2 + D + d] : 0.f;
-    qv[d] = (d < D) ? fmaf(Pt, (-2.f * q.u[d] + q.g[d]) / Dc, phi.d[1 + d]) : 0.f;
-  }
+  float Prho, Pu[3], Pt, PF[3];
+  phi_grad<L>(M, q.rho, q.u, q.tb, q.F, a.thermal != 0, a.omega, a.beta, Prho, Pu, Pt, PF);
+  float qv[3];
+  for (int d = 0; d < 3; ++d) qv[d] = (d < D) ? fmaf(Pt, (-2.f * q.u[d] + q.g[d]) / Dc, Pu[d]) : 0.f;
   const float inv_rho = 1.f / q.rho;
   float dj[3], dg[3], qj = 0.f, Fg = 0.f;
   for (int d = 0; d < 3; ++d) {
