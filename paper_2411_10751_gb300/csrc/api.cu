@@ -53,11 +53,14 @@ struct hlbm_ctx {
   // graphs replaying kGraphSteps steps from buffer parity 0 / 1
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
-  // TMA staging of interior tiles (D2Q37): tensor maps per (buffer, box)
+  // TMA staging: tensor maps per (population buffer address, box); the
+  // buffers are the context's two and, during hlbm_adjoint_run, its
+  // workspace's recomputed states
   bool tma_ok = false;
   bool tma_store_ok = false;
   struct TMap {
-    int buf, wb, hb;
+    const void* base;
+    int wb, hb;
     CUtensorMap map;
   };
   std::deque<TMap> tmaps;         // deque: pointers to entries stay valid as maps are added
@@ -250,13 +253,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // wb x hb x 1 box (D2Q37), or as [Q][nz][ny][nx] with a wb x hb x 1 x 1 box
 // (D3Q39); null if it cannot be encoded (the kernels then stage every tile
 // with plain loads).
-const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
+const CUtensorMap* tensor_map_at(hlbm_ctx* c, const void* base, int wb, int hb) {
   for (auto& t : c->tmaps)
-    if (t.buf == buf && t.wb == wb && t.hb == hb) return &t.map;
+    if (t.base == base && t.wb == wb && t.hb == hb) return &t.map;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return nullptr;
   hlbm_ctx::TMap t{};
-  t.buf = buf;
+  t.base = base;
   t.wb = wb;
   t.hb = hb;
   const CUtensorMapDataType dt = c->storage == ST_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -270,7 +273,8 @@ const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
   const cuuint64_t strides3[3] = {(cuuint64_t)c->nx * e, (cuuint64_t)c->nx * c->ny * e, (cuuint64_t)c->N * e};
   const cuuint32_t box[4] = {(cuuint32_t)wb, (cuuint32_t)hb, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = enc(&t.map, dt, d3 ? 4 : 3, c->pop[buf], d3 ? dims3 : dims2, d3 ? strides3 : strides2, box, estr,
+  CUresult r = enc(&t.map, dt, d3 ? 4 : 3, const_cast<void*>(base), d3 ? dims3 : dims2, d3 ? strides3 : strides2,
+                   box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return nullptr;
@@ -278,15 +282,16 @@ const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) {
   return &c->tmaps.back().map;
 }
 
+const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) { return tensor_map_at(c, c->pop[buf], wb, hb); }
+
 cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
   if (c->lattice != 0) {
     // persistent whole-row kernel: box of 256 / nx rows, and single rows
     CUtensorMap maps3[2];
     const CUtensorMap* tm = nullptr;
     if (!moments && a.persistent && a.tma && (c->nx == 32 || c->nx == 64 || c->nx == 128 || c->nx == 256)) {
-      const int buf = (a.fin == c->pop[0]) ? 0 : 1;
-      const CUtensorMap* mb = tensor_map(c, buf, c->nx, 256 / c->nx);
-      const CUtensorMap* mr = tensor_map(c, buf, c->nx, 1);
+      const CUtensorMap* mb = tensor_map_at(c, a.fin, c->nx, 256 / c->nx);
+      const CUtensorMap* mr = tensor_map_at(c, a.fin, c->nx, 1);
       if (mb && mr) {
         maps3[0] = *mb;
         maps3[1] = *mr;
@@ -301,9 +306,8 @@ cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
   if (a.tma) {
     int wb = 0, hb = 0, ob = 0;
     step_box_d2q37(c->kind, c->storage, moments, c->rows, &wb, &hb, &ob);
-    const int buf = (a.fin == c->pop[0]) ? 0 : 1;
-    const CUtensorMap* in = tensor_map(c, buf, wb, hb);
-    const CUtensorMap* out = moments ? nullptr : tensor_map(c, buf ^ 1, 32, ob);
+    const CUtensorMap* in = tensor_map_at(c, a.fin, wb, hb);
+    const CUtensorMap* out = moments ? nullptr : tensor_map_at(c, a.fout, 32, ob);
     if (in) maps[0] = *in;
     else a.tma = 0;
     if (out && c->tma_store_ok) {
@@ -730,6 +734,11 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   const int K = std::min(ckpt_every, steps);
   const AdjLayout L = adj_layout(c, steps, K);
   if (bytes < L.total) return fail(c, HLBM_ENOMEM, "adjoint workspace smaller than hlbm_adjoint_workspace_bytes()");
+  // tensor maps of an earlier run's workspace slots are of no further use
+  std::deque<hlbm_ctx::TMap> keep;
+  for (const auto& t : c->tmaps)
+    if (t.base == c->pop[0] || t.base == c->pop[1]) keep.push_back(t);
+  c->tmaps.swap(keep);
   char* ws = static_cast<char*>(workspace);
   auto state = [&](size_t k) { return static_cast<void*>(ws + k * L.state); };
   float* lam[2] = {reinterpret_cast<float*>(ws + L.off_lam0), reinterpret_cast<float*>(ws + L.off_lam1)};
@@ -757,8 +766,7 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
     // states of the segment: j = 0 is checkpoint k, j >= 1 are recomputed into slots nseg + j - 1
     auto seg = [&](int j) { return j == 0 ? state(k) : state((size_t)nseg + j - 1); };
     for (int j = 1; j < len; ++j) {
-      StepArgs a = make_args(c);
-      a.tma = 0;
+      StepArgs a = make_args(c);   // staged by tensor maps of the workspace slots
       a.fin = seg(j - 1);
       a.fout = seg(j);
       HLBM_CUDA(c, launch_step(c, a, false), "recompute step");
