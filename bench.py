@@ -417,6 +417,8 @@ def main():
                     help="device-timed steps only (no e2e, variants, extras or CPU baseline; for profiling)")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="run the adjoint extra alone and print its line (for profiling)")
+    ap.add_argument("--adjoint-steps", type=int, default=400, help="T of the adjoint line")
+    ap.add_argument("--adjoint-ckpt", type=int, default=50, help="checkpoint interval of the adjoint line")
     args = ap.parse_args()
     if args.only_device:
         args.no_variants = args.no_extras = args.no_cpu_baseline = True
@@ -438,7 +440,7 @@ def main():
     pkg.load()
     if args.only_adjoint:
         if rank == 0:
-            print(json.dumps({"adjoint": adjoint_extra(lrank)}))
+            print(json.dumps({"adjoint": adjoint_extra(lrank, steps=args.adjoint_steps, ckpt=args.adjoint_ckpt)}))
         return 0
 
     case = WORKLOADS[args.workload][0]()

@@ -22,6 +22,7 @@
 #include "hlbm.h"
 #include "internal.h"
 #include "step_common.cuh"
+#include "tma.cuh"
 
 namespace hlbm {
 namespace {
@@ -180,6 +181,9 @@ struct AdjArgs {
   int nx, ny, nz;
   float rho0, omega, beta;
   int thermal;
+  int* status;                  // whole-row kernel: HLBM_ETIMEOUT when a copy wait gives up
+  unsigned long long wait_ns;   // bound of each copy wait
+  unsigned long long* ctr;      // whole-row kernel: tile counter; each launch takes tiles + CTAs values
 };
 
 // node quantities of f_n(x): rho, j, e, u, tb, F with the forward kernel's arithmetic
@@ -188,12 +192,12 @@ struct NodeQ {
   float rho, j[3], e, u[3], tb, F[3], g[3];
 };
 
-template <class L, class C>
-__device__ __forceinline__ NodeQ<L> node_q(const AdjArgs& a, int x, int y, int z, int node) {
+// from the node's pulled populations gv (overwritten) and its acceleration
+// (component d: gn(d), read after the moments)
+template <class L, class GN>
+__device__ __forceinline__ NodeQ<L> node_q_from(const AdjArgs& a, float (&gv)[L::Q], GN&& gn) {
   constexpr int D = L::D;
   constexpr float Dc = (float)(D * L::cs2);
-  float gv[L::Q];
-  gather<L, C>(static_cast<const typename C::T*>(a.fwd), a.N, a.nx, a.ny, a.nz, x, y, z, gv);
   float dr, acc, J[3], Pih;
   moments_h<L>(gv, dr, acc, J, Pih);
   NodeQ<L> q;
@@ -201,7 +205,7 @@ __device__ __forceinline__ NodeQ<L> node_q(const AdjArgs& a, int x, int y, int z
   q.e = fmaf(Dc, q.rho, Pih);
   float uu = 0.f, ug = 0.f;
   for (int d = 0; d < 3; ++d) {
-    q.g[d] = (d < D) ? __ldg(a.gfield + (size_t)d * a.N + node) : 0.f;
+    q.g[d] = (d < D) ? gn(d) : 0.f;
     q.j[d] = (d < D) ? J[d] : 0.f;
     q.F[d] = q.rho * q.g[d];
     q.u[d] = fmaf(0.5f, q.F[d], q.j[d]) / q.rho;
@@ -211,6 +215,13 @@ __device__ __forceinline__ NodeQ<L> node_q(const AdjArgs& a, int x, int y, int z
   // theta-bar = (e - rho |u|^2 + rho u.g) / (rho D c0^2) - 1 (Eq. 4.5, G2 = 2 u.F)
   q.tb = a.thermal ? (Pih - q.rho * uu + q.rho * ug) / (q.rho * Dc) : 0.f;
   return q;
+}
+
+template <class L, class C>
+__device__ __forceinline__ NodeQ<L> node_q(const AdjArgs& a, int x, int y, int z, int node) {
+  float gv[L::Q];
+  gather<L, C>(static_cast<const typename C::T*>(a.fwd), a.N, a.nx, a.ny, a.nz, x, y, z, gv);
+  return node_q_from<L>(a, gv, [&](int d) { return __ldg(a.gfield + (size_t)d * a.N + node); });
 }
 
 template <class L>
@@ -260,6 +271,43 @@ __global__ void __launch_bounds__(256) adjoint_seed_kernel(const __grid_constant
   }
 }
 
+// lambda_n (stored) and the dL/dg increment dg at one node from its forward
+// quantities q and mu_i = lambda_{n+1,i}(x + c_i)
+template <class L>
+__device__ __forceinline__ void reverse_node(const AdjArgs& a, const NodeQ<L>& q, const float (&mu)[L::Q], long long n,
+                                             float (&dg)[3]) {
+  using A = AdjCfg<L>;
+  constexpr int D = L::D;
+  constexpr float Dc = (float)(D * L::cs2);
+  float M[A::NM];
+  hermite_moments<L>(mu, M);
+  float Prho, Pu[3], Pt, PF[3];
+  phi_grad<L>(M, q.rho, q.u, q.tb, q.F, a.thermal != 0, a.omega, a.beta, Prho, Pu, Pt, PF);
+  float qv[3];
+  for (int d = 0; d < 3; ++d) qv[d] = (d < D) ? fmaf(Pt, (-2.f * q.u[d] + q.g[d]) / Dc, Pu[d]) : 0.f;
+  const float inv_rho = 1.f / q.rho;
+  float dj[3], qj = 0.f, Fg = 0.f;
+  for (int d = 0; d < 3; ++d) {
+    dj[d] = qv[d] * inv_rho;
+    qj = fmaf(qv[d], q.j[d], qj);
+    Fg = fmaf(PF[d], q.g[d], Fg);
+    dg[d] = q.rho * PF[d] + 0.5f * qv[d] + Pt * q.u[d] / Dc;
+  }
+  const float de = Pt * inv_rho / Dc;
+  const float drho = Prho + Fg - qj * inv_rho * inv_rho - Pt * q.e * inv_rho * inv_rho / Dc;
+  const float om1 = 1.f - a.omega;
+  static_for<L::Q>([&](auto I) {
+    constexpr int i = I;
+    float v = fmaf(om1, mu[i], drho);
+    static_for<D>([&](auto Ax) {
+      constexpr int ax = Ax;
+      if constexpr (L::c(i, ax) != 0) v = fmaf((float)L::c(i, ax), dj[ax], v);
+    });
+    if constexpr (L::norm2(i) != 0) v = fmaf((float)L::norm2(i), de, v);
+    a.lam_out[(size_t)i * a.N + n] = v;
+  });
+}
+
 // one reverse step: lambda_n from lambda_{n+1}, accumulating dL/dg
 template <class L, int ST>
 __global__ void __launch_bounds__(128) adjoint_step_kernel(const __grid_constant__ AdjArgs a) {
@@ -288,39 +336,196 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(const __grid_constant
       mu[i] = __ldg(a.lam_in + (size_t)i * a.N + off);
     });
   }
-  float M[A::NM];
-  hermite_moments<L>(mu, M);
-  float Prho, Pu[3], Pt, PF[3];
-  phi_grad<L>(M, q.rho, q.u, q.tb, q.F, a.thermal != 0, a.omega, a.beta, Prho, Pu, Pt, PF);
-  float qv[3];
-  for (int d = 0; d < 3; ++d) qv[d] = (d < D) ? fmaf(Pt, (-2.f * q.u[d] + q.g[d]) / Dc, Pu[d]) : 0.f;
-  const float inv_rho = 1.f / q.rho;
-  float dj[3], dg[3], qj = 0.f, Fg = 0.f;
-  for (int d = 0; d < 3; ++d) {
-    dj[d] = qv[d] * inv_rho;
-    qj = fmaf(qv[d], q.j[d], qj);
-    Fg = fmaf(PF[d], q.g[d], Fg);
-    dg[d] = q.rho * PF[d] + 0.5f * qv[d] + Pt * q.u[d] / Dc;
-  }
-  const float de = Pt * inv_rho / Dc;
-  const float drho = Prho + Fg - qj * inv_rho * inv_rho - Pt * q.e * inv_rho * inv_rho / Dc;
-  const float om1 = 1.f - a.omega;
-  static_for<L::Q>([&](auto I) {
-    constexpr int i = I;
-    float v = fmaf(om1, mu[i], drho);
-    static_for<D>([&](auto Ax) {
-      constexpr int ax = Ax;
-      if constexpr (L::c(i, ax) != 0) v = fmaf((float)L::c(i, ax), dj[ax], v);
-    });
-    if constexpr (L::norm2(i) != 0) v = fmaf((float)L::norm2(i), de, v);
-    a.lam_out[(size_t)i * a.N + n] = v;
-  });
+  float dg[3];
+  reverse_node<L>(a, q, mu, n, dg);
   for (int d = 0; d < D; ++d) a.dLdg[(size_t)d * a.N + n] += dg[d];
 }
 
+// Persistent D3Q39 reverse step on tiles of 256 nodes spanning whole x-rows
+// (a tile is 256 / nx rows of one z-plane).  Plane i of the forward state
+// (pulled: f_i(x) = S_i(x - c_i)) is the 4D box at (0, y0 - c_y, z - c_z) and
+// plane i of lambda_{n+1} (mu_i(x) = lambda_i(x + c_i)) the box at
+// (0, y0 + c_y, z + c_z); the x shifts are index masks in shared memory, the
+// z wrap a wrapped coordinate, and a plane whose rows cross the y-edge is
+// copied row by row.  The tile's acceleration comes with the same barrier,
+// and its dL/dg increment goes back as one bulk reduce-add per component, so
+// the arithmetic waits on no global load.  Tiles come in order from the
+// device counter; once a tile is in registers the CTA takes the next index
+// and issues its copies (threads 0..38 the forward planes, 128..166 the
+// lambda planes, 64..66 the acceleration), so they overlap the arithmetic and
+// the stores.  One node per thread.
+constexpr int kAdjRowNodes = 256;
+
+template <int ST>
+struct AdjRowsSmem {
+  static constexpr int TN = kAdjRowNodes, Q = D3Q39::Q;
+  static constexpr int LAM = 0;                                                // lambda_{n+1} planes (FP32)
+  static constexpr int FWD = LAM + Q * TN * 4;                                 // forward-state planes
+  static constexpr int G = FWD + Q * TN * (int)sizeof(typename Codec<ST>::T);  // acceleration [3][TN]
+  static constexpr int DG = G + 3 * TN * 4;                                    // dL/dg increment [3][TN]
+  static constexpr int BAR = DG + 3 * TN * 4;
+  static constexpr int BYTES = BAR + 16;
+  static constexpr uint32_t TX = (uint32_t)DG;                                 // bytes landing per tile
+};
+
+template <int ST>
+__global__ void __launch_bounds__(256, 2)
+    adjoint_rows_kernel(const __grid_constant__ AdjArgs a, const __grid_constant__ CUtensorMap tm_fb,
+                        const __grid_constant__ CUtensorMap tm_fr, const __grid_constant__ CUtensorMap tm_lb,
+                        const __grid_constant__ CUtensorMap tm_lr, const __grid_constant__ CUtensorMap tm_g,
+                        const __grid_constant__ CUtensorMap tm_dg) {
+  using L = D3Q39;
+  using T = typename Codec<ST>::T;
+  using S = AdjRowsSmem<ST>;
+  constexpr int TN = kAdjRowNodes;
+  constexpr int RED = 96;   // the thread that issues the dL/dg reductions
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_next[2];
+  float* sl = reinterpret_cast<float*>(smem + S::LAM);
+  T* sf = reinterpret_cast<T*>(smem + S::FWD);
+  float* sg = reinterpret_cast<float*>(smem + S::G);
+  float* sdg = reinterpret_cast<float*>(smem + S::DG);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR);
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int by = TN / nx;
+  const int nty = (ny + by - 1) / by;
+  const int ntiles = nty * nz;
+  const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
+  const int tid = threadIdx.x, xm = nx - 1;
+  const int xk = tid & xm, rk = tid / nx;
+  const bool isf = tid < L::Q, isl = tid >= 128 && tid < 128 + L::Q, isg = tid >= 64 && tid < 67;
+  const int p = isf ? tid : (isl ? tid - 128 : tid - 64);   // the plane this thread copies
+  int pcy = 0, pcz = 0;
+  if (isf || isl) d3_cyz(p, pcy, pcz, typename make_iseq<L::Q>::type{});
+  // this thread's plane of tile t into shared memory (the barrier is armed)
+  auto issue_plane = [&](int t) {
+    const int z = t / nty, y0 = (t - z * nty) * by;
+    fence_proxy_async_smem();
+    if (isf) {
+      const int zz = wrap_near3(z - pcz, nz), ys = y0 - pcy;
+      if (ys >= 0 && ys + by <= ny) {
+        tma_load_4d(sf + p * TN, &tm_fb, 0, ys, zz, p, bar);
+      } else {
+        for (int r = 0; r < by; ++r)
+          tma_load_4d(sf + p * TN + r * nx, &tm_fr, 0, ((ys + r) % ny + ny) % ny, zz, p, bar);
+      }
+    } else if (isl) {
+      const int zz = wrap_near3(z + pcz, nz), ys = y0 + pcy;
+      if (ys >= 0 && ys + by <= ny) {
+        tma_load_4d(sl + p * TN, &tm_lb, 0, ys, zz, p, bar);
+      } else {
+        for (int r = 0; r < by; ++r)
+          tma_load_4d(sl + p * TN + r * nx, &tm_lr, 0, ((ys + r) % ny + ny) % ny, zz, p, bar);
+      }
+    } else if (isg) {
+      tma_load_4d(sg + p * TN, &tm_g, 0, y0, z, p, bar);   // rows past the y-edge read as zero
+    }
+  };
+  // tid 0: takes the next tile index into slot `slot` and arms the barrier for it
+  auto take = [&](int slot) {
+    const int t = (int)(atomicAdd(a.ctr, 1ull) % period);
+    s_next[slot] = t;
+    if (t < ntiles) mbar_arrive_expect_tx(bar, S::TX);
+  };
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    take(0);
+  }
+  __syncthreads();
+  int t = s_next[0];
+  if (t < ntiles && (isf || isl || isg)) issue_plane(t);
+  uint32_t phase = 0;
+  for (int it = 1; t < ntiles; ++it) {
+    const int z = t / nty, y0 = (t - z * nty) * by;
+    const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
+      mbar_wait_bounded(bar, phase, a.wait_ns);
+      if (tid == RED) bulk_wait_all();
+      __syncthreads();
+      return;
+    }
+    phase ^= 1u;
+    if (tid == 0) take(it & 1);   // the barrier's next phase belongs to the next tile
+    float gv[L::Q], mu[L::Q], gn[3];
+    static_for<L::Q>([&](auto I) {
+      constexpr int i = I;
+      constexpr int cx = L::c(i, 0);
+      gv[i] = to_float(sf[i * TN + rk * nx + ((xk - cx) & xm)]);
+      mu[i] = sl[i * TN + rk * nx + ((xk + cx) & xm)];
+    });
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gn[d] = sg[d * TN + tid];
+    if (tid == RED) bulk_wait_read_all();   // the previous tile's reductions have read their source
+    __syncthreads();  // the staging buffers are free and the next index is published
+    const int tn = s_next[it & 1];
+    if (tn < ntiles && (isf || isl || isg)) issue_plane(tn);
+    const int y = y0 + rk;
+    float dg[3] = {0.f, 0.f, 0.f};
+    if (y < ny) {
+      const long long n = ((long long)z * ny + y) * nx + xk;
+      const NodeQ<L> q = node_q_from<L>(a, gv, [&](int d) { return gn[d]; });
+      reverse_node<L>(a, q, mu, n, dg);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sdg[d * TN + tid] = dg[d];
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == RED) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) tma_reduce_add_4d(&tm_dg, sdg + d * TN, 0, y0, z, d);   // rows past the edge are skipped
+      bulk_commit();
+    }
+    t = tn;
+  }
+  if (tid == RED) bulk_wait_all();
+}
+
+// Whether the whole-row kernel serves this domain (rows of the stored type
+// fill 128 bytes, so single-row copies land on 128-byte aligned addresses).
+template <int ST>
+bool adj_rows_eligible(const AdjArgs& a) {
+  return (a.nx == 32 || a.nx == 64 || a.nx == 128 || a.nx == 256) &&
+         a.nx * (int)sizeof(typename Codec<ST>::T) >= 128;
+}
+
+template <int ST>
+int adj_rows_ctas() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(adjoint_rows_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjRowsSmem<ST>::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adjoint_rows_kernel<ST>, 256, AdjRowsSmem<ST>::BYTES);
+    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return n;
+}
+
+template <int ST>
+cudaError_t launch_adj_step(const AdjArgs& a, const CUtensorMap* tm, cudaStream_t s) {
+  if (tm && a.ctr && adj_rows_eligible<ST>(a)) {
+    const int tiles = ((a.ny + kAdjRowNodes / a.nx - 1) / (kAdjRowNodes / a.nx)) * a.nz;
+    const int ctas = std::min(tiles, adj_rows_ctas<ST>());
+    adjoint_rows_kernel<ST><<<ctas, 256, AdjRowsSmem<ST>::BYTES, s>>>(a, tm[0], tm[1], tm[2], tm[3], tm[4], tm[5]);
+  } else {
+    adjoint_step_kernel<D3Q39, ST><<<(unsigned)((a.N + 127) / 128), 128, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 template <class L>
-cudaError_t launch_adj(int storage, bool seed, const AdjArgs& a, cudaStream_t s) {
+cudaError_t launch_adj(int storage, bool seed, const AdjArgs& a, const CUtensorMap* tm, cudaStream_t s) {
   const unsigned b256 = (unsigned)((a.N + 255) / 256), b128 = (unsigned)((a.N + 127) / 128);
+  if constexpr (L::D == 3) {
+    if (!seed) {
+      if (storage == ST_F32) return launch_adj_step<ST_F32>(a, tm, s);
+      if (storage == ST_F16) return launch_adj_step<ST_F16>(a, tm, s);
+      return launch_adj_step<ST_BF16>(a, tm, s);
+    }
+  }
   switch (storage) {
     case ST_F32:
       if (seed) adjoint_seed_kernel<L, ST_F32><<<b256, 256, 0, s>>>(a);
@@ -342,7 +547,7 @@ cudaError_t launch_adj(int storage, bool seed, const AdjArgs& a, cudaStream_t s)
 
 cudaError_t launch_adjoint(int lattice, int storage, bool seed, const void* fwd, const float* lam_in, float* lam_out,
                            const float* gfield, float* dLdg, double* partials, long long N, int nx, int ny, int nz,
-                           float rho0, float omega, float beta, int thermal, cudaStream_t s) {
+                           float rho0, float omega, float beta, int thermal, const AdjRows& rows, cudaStream_t s) {
   AdjArgs a{};
   a.fwd = fwd;
   a.lam_in = lam_in;
@@ -358,7 +563,11 @@ cudaError_t launch_adjoint(int lattice, int storage, bool seed, const void* fwd,
   a.omega = omega;
   a.beta = beta;
   a.thermal = thermal;
-  return lattice == 0 ? launch_adj<D2Q37>(storage, seed, a, s) : launch_adj<D3Q39>(storage, seed, a, s);
+  a.status = rows.status;
+  a.wait_ns = rows.wait_ns;
+  a.ctr = rows.ctr;
+  return lattice == 0 ? launch_adj<D2Q37>(storage, seed, a, nullptr, s)
+                      : launch_adj<D3Q39>(storage, seed, a, rows.tmaps, s);
 }
 
 int adjoint_seed_blocks(long long N) { return (int)((N + 255) / 256); }

@@ -61,11 +61,14 @@ struct hlbm_ctx {
   struct TMap {
     const void* base;
     int wb, hb;
+    bool f32;    // viewed as FP32 (the adjoint's lambda) instead of the storage type
+    int planes;  // outermost extent: Q, or D for a per-node vector field
     CUtensorMap map;
   };
   std::deque<TMap> tmaps;         // deque: pointers to entries stay valid as maps are added
   int* status = nullptr;          // device status word (bounded waits)
   unsigned long long* tile_ctr = nullptr;  // persistent step's tile counter
+  unsigned long long* adj_ctr = nullptr;   // whole-row reverse step's tile counter
   bool ctr_reset = true;          // the counter must be zeroed before the next step
   unsigned long long wait_ns = 2000000000ull;
   int debug_skip_tma = 0;
@@ -186,6 +189,7 @@ void carve(hlbm_ctx* c) {
   c->red = reinterpret_cast<double*>(c->arena + L.off_red);
   c->status = reinterpret_cast<int*>(c->arena + L.off_red + 64);
   c->tile_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 128);
+  c->adj_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 192);
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -251,25 +255,29 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Tensor map of population buffer `buf` viewed as [Q][ny][nx] with a
 // wb x hb x 1 box (D2Q37), or as [Q][nz][ny][nx] with a wb x hb x 1 x 1 box
-// (D3Q39); null if it cannot be encoded (the kernels then stage every tile
-// with plain loads).
-const CUtensorMap* tensor_map_at(hlbm_ctx* c, const void* base, int wb, int hb) {
+// (D3Q39), in the storage type or (f32) in FP32, with `planes` instead of Q
+// outermost when given (a [D][N] FP32 field); null if it cannot be encoded
+// (the kernels then stage every tile with plain loads).
+const CUtensorMap* tensor_map_at(hlbm_ctx* c, const void* base, int wb, int hb, bool f32 = false, int planes = 0) {
+  if (planes <= 0) planes = c->Q;
   for (auto& t : c->tmaps)
-    if (t.base == base && t.wb == wb && t.hb == hb) return &t.map;
+    if (t.base == base && t.wb == wb && t.hb == hb && t.f32 == f32 && t.planes == planes) return &t.map;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return nullptr;
   hlbm_ctx::TMap t{};
   t.base = base;
   t.wb = wb;
   t.hb = hb;
-  const CUtensorMapDataType dt = c->storage == ST_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                 : c->storage == ST_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  t.f32 = f32;
+  t.planes = planes;
+  const CUtensorMapDataType dt = (f32 || c->storage == ST_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : c->storage == ST_F16        ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const bool d3 = c->lattice == HLBM_D3Q39;
-  const cuuint64_t e = (cuuint64_t)c->elem;
-  const cuuint64_t dims2[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->Q};
+  const cuuint64_t e = f32 ? 4 : (cuuint64_t)c->elem;
+  const cuuint64_t dims2[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)planes};
   const cuuint64_t strides2[2] = {(cuuint64_t)c->nx * e, (cuuint64_t)c->N * e};
-  const cuuint64_t dims3[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)c->Q};
+  const cuuint64_t dims3[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)planes};
   const cuuint64_t strides3[3] = {(cuuint64_t)c->nx * e, (cuuint64_t)c->nx * c->ny * e, (cuuint64_t)c->N * e};
   const cuuint32_t box[4] = {(cuuint32_t)wb, (cuuint32_t)hb, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -755,8 +763,32 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
     c->steps += len;
   }
   // seed from the final state: lambda_T, dL/dg at T, kinetic energy
+  const AdjRows gather_only{nullptr, c->status, c->wait_ns, nullptr};
   HLBM_CUDA(c, launch_adjoint(c->lattice, c->storage, true, c->pop[c->cur], nullptr, lam[0], c->gfield, dLdg, part,
-                              c->N, c->nx, c->ny, c->nz, rho0, omega, beta, thermal, c->stream), "adjoint seed");
+                              c->N, c->nx, c->ny, c->nz, rho0, omega, beta, thermal, gather_only, c->stream),
+            "adjoint seed");
+  // D3Q39 whole-row reverse kernel: tiles of 256 / nx rows; maps of the
+  // forward state (box, row), of lambda_{n+1} (box, row), of the acceleration
+  // and of dL/dg (boxes) per launch
+  const bool rows = c->lattice == HLBM_D3Q39 && c->tma_ok &&
+                    (c->nx == 32 || c->nx == 64 || c->nx == 128 || c->nx == 256) &&
+                    (reinterpret_cast<uintptr_t>(dLdg) & 15) == 0;
+  if (rows) HLBM_CUDA(c, cudaMemsetAsync(c->adj_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
+  auto rows_of = [&](const void* fwd, const float* lin, CUtensorMap (&m)[6]) {
+    AdjRows r{nullptr, c->status, c->wait_ns, c->adj_ctr};
+    if (!rows) return r;
+    const int hb = 256 / c->nx;
+    const CUtensorMap* p[6] = {tensor_map_at(c, fwd, c->nx, hb), tensor_map_at(c, fwd, c->nx, 1),
+                               tensor_map_at(c, lin, c->nx, hb, true), tensor_map_at(c, lin, c->nx, 1, true),
+                               tensor_map_at(c, c->gfield, c->nx, hb, true, 3),
+                               tensor_map_at(c, dLdg, c->nx, hb, true, 3)};
+    for (int i = 0; i < 6; ++i) {
+      if (!p[i]) return r;
+      m[i] = *p[i];
+    }
+    r.tmaps = m;
+    return r;
+  };
   const int nb = adjoint_seed_blocks(c->N);
   HLBM_CUDA(c, launch_reduce_partials(part, nb, part + (size_t)nb * 8, c->stream), "reduce");
   int cur = 0;
@@ -772,8 +804,10 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
       HLBM_CUDA(c, launch_step(c, a, false), "recompute step");
     }
     for (int j = len - 1; j >= 0; --j) {
+      CUtensorMap m[6];
+      const AdjRows r = rows_of(seg(j), lam[cur], m);
       HLBM_CUDA(c, launch_adjoint(c->lattice, c->storage, false, seg(j), lam[cur], lam[cur ^ 1], c->gfield, dLdg,
-                                  nullptr, c->N, c->nx, c->ny, c->nz, rho0, omega, beta, thermal, c->stream),
+                                  nullptr, c->N, c->nx, c->ny, c->nz, rho0, omega, beta, thermal, r, c->stream),
                 "adjoint step");
       cur ^= 1;
     }

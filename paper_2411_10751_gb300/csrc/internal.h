@@ -86,9 +86,19 @@ int moment_blocks(int lattice, int nx, int ny, int nz);
 // per-block kinetic-energy sums (adjoint_seed_blocks(N) blocks, stride 8) from
 // the state `fwd`; otherwise one reverse step lam_in -> lam_out with the
 // forward state `fwd` whose gather is f_n, accumulating dL/dg.
+// rows: the D3Q39 whole-row reverse kernel's tensor maps (forward state box
+// and row, lambda_{n+1} box and row, acceleration box, dL/dg box; null: the
+// gather kernel), status word,
+// wait bound and tile counter (zero before the first reverse step of a run).
+struct AdjRows {
+  const CUtensorMap* tmaps;
+  int* status;
+  unsigned long long wait_ns;
+  unsigned long long* ctr;
+};
 cudaError_t launch_adjoint(int lattice, int storage, bool seed, const void* fwd, const float* lam_in, float* lam_out,
                            const float* gfield, float* dLdg, double* partials, long long N, int nx, int ny, int nz,
-                           float rho0, float omega, float beta, int thermal, cudaStream_t s);
+                           float rho0, float omega, float beta, int thermal, const AdjRows& rows, cudaStream_t s);
 int adjoint_seed_blocks(long long N);
 
 }  // namespace hlbm

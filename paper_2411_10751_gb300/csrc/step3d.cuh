@@ -153,14 +153,6 @@ constexpr int rows3_smem() {
   return D3Q39::Q * kRows3Nodes * (int)sizeof(typename Codec<ST>::T) + 16;
 }
 
-// c_y, c_z of D3Q39 velocity p for a runtime p (a fold over the compile-time
-// table; each issuing thread does one lookup).
-template <int... I>
-__device__ __forceinline__ void d3_cyz(int p, int& cy, int& cz, iseq<I...>) {
-  ((cy = (p == I) ? D3Q39::c(I, 1) : cy), ...);
-  ((cz = (p == I) ? D3Q39::c(I, 2) : cz), ...);
-}
-
 template <int ST>
 __global__ void __launch_bounds__(128, 3)
     step3d_rows_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tm_box,
@@ -303,9 +295,13 @@ __global__ void __launch_bounds__(128, 3)
   }
 }
 
-// Whether the whole-row persistent kernel serves this domain.
+// Whether the whole-row persistent kernel serves this domain: a row of the
+// stored type must fill 128 bytes so that the single-row copies land on
+// 128-byte aligned shared-memory addresses (16-bit storage from nx = 64).
+template <int ST>
 inline bool rows3_eligible(const StepArgs& a) {
-  return a.tma && (a.nx == 32 || a.nx == 64 || a.nx == 128 || a.nx == 256);
+  return a.tma && (a.nx == 32 || a.nx == 64 || a.nx == 128 || a.nx == 256) &&
+         a.nx * (int)sizeof(typename Codec<ST>::T) >= 128;
 }
 
 template <int ST>
@@ -328,7 +324,7 @@ template <int ST>
 cudaError_t launch_step3d_st(const StepArgs& a, int kind, bool mom, int rows, int npt, const CUtensorMap* tmaps,
                              cudaStream_t s) {
   if (kind != KIND_LOCAL) return cudaErrorInvalidValue;
-  if (!mom && a.persistent && tmaps && rows3_eligible(a)) {
+  if (!mom && a.persistent && tmaps && rows3_eligible<ST>(a)) {
     const int by = kRows3Nodes / a.nx;
     const int tiles = ((a.ny + by - 1) / by) * a.nz;
     const int ctas = std::min(tiles, rows3_ctas<ST>());

@@ -60,6 +60,14 @@ template <> struct Codec<ST_BF16> {
 __device__ __forceinline__ float to_float(float v) { return v; }
 __device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// c_y, c_z of D3Q39 velocity p for a runtime p (a fold over the compile-time
+// table; each thread that issues a plane's copies does one lookup).
+template <int... I>
+__device__ __forceinline__ void d3_cyz(int p, int& cy, int& cz, iseq<I...>) {
+  ((cy = (p == I) ? D3Q39::c(I, 1) : cy), ...);
+  ((cz = (p == I) ? D3Q39::c(I, 2) : cz), ...);
+}
 // exact for values that came from to_float of the same type
 template <class T> __device__ __forceinline__ T from_float(float v);
 template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }

@@ -65,12 +65,18 @@ def _ref(c, steps):
     return adjoint.kinetic_energy_gradient(L, c.rho.shape, c.tau_hat, o.f, c.gfield, steps)
 
 
-@pytest.mark.parametrize("which", ["d3q39_16", "d3q39_ragged", "d2q37"])
+@pytest.mark.parametrize("which", ["d3q39_16", "d3q39_ragged", "d3q39_rows32", "d3q39_rows64", "d2q37"])
 def test_adjoint_matches_oracle(HLBM, which):
+    """d3q39_rows32/64: the whole-row reverse kernel (nx 32 and 64) on ragged
+    y (a last tile with rows past the edge, planes copied row by row)."""
     if which == "d3q39_16":
         c, steps, K = _case3d(), 20, 6
     elif which == "d3q39_ragged":
         c, steps, K = _case3d(n=24, nx=21, ny=11, nz=9), 16, 5
+    elif which == "d3q39_rows32":
+        c, steps, K = _case3d(n=32, nx=32, ny=11, nz=9), 12, 5
+    elif which == "d3q39_rows64":
+        c, steps, K = _case3d(n=64, nx=64, ny=10, nz=7), 8, 3
     else:
         c, steps, K = _case2d(), 30, 7
     loss, grad = _gpu(HLBM, c, steps, K)
@@ -78,6 +84,23 @@ def test_adjoint_matches_oracle(HLBM, which):
     assert abs(loss - lref) < 1e-5 * abs(lref), (loss, lref)
     err = np.abs(grad - gref).max() / np.abs(gref).max()
     assert err < 1e-4, err
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_reduced_storage_adjoint(HLBM, storage):
+    """16-bit stored forward states (whole-row reverse kernel at nx = 64): the
+    gradient stays within the storage rounding of the FP64 one."""
+    c, steps, K = _case3d(n=64, nx=64, ny=10, nz=7), 8, 3
+    g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, storage=storage)
+    g.set_force_field(c.gfield, "field")
+    g.init(c.rho, c.u, c.theta)
+    loss, grad = g.adjoint(steps, K)
+    grad = grad.cpu().numpy()
+    g.close()
+    lref, gref = _ref(c, steps)
+    err = np.abs(grad - gref).max() / np.abs(gref).max()
+    print(storage, "adjoint rel err", err, abs(loss - lref) / abs(lref))
+    assert err < 5e-2, err
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(HLBM):
