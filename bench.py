@@ -92,6 +92,25 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def _multistep(case, sched) -> bool:
+    """Whether this schedule runs the multi-step kernel on this workload
+    (D2Q37, persistent = 3, tiles covering the domain exactly)."""
+    if case.lattice != "D2Q37" or sched[2] != 3:
+        return False
+    h = 3 if case.params.get("SC") else (1 if case.params.get("H") else 0)
+    return case.nx % 32 == 0 and case.ny % sched[0] == 0 and h + 3 <= sched[0]
+
+
+def _launches(case, sched, steps) -> int:
+    """Step-kernel launches of hlbm_step(steps): one per step, or one per
+    block of up to 1024 steps for the multi-step kernel."""
+    if not _multistep(case, sched):
+        return steps
+    tiles = (case.nx // 32) * (case.ny // sched[0])
+    smax = max(1, min(1024, (2 ** 31 - 1) // tiles))
+    return -(-steps // smax)
+
+
 def _ncu_traffic(kernel_hash: str, storage: str, schedule):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     if it was captured from the current kernel sources with this schedule;
@@ -107,7 +126,8 @@ def _ncu_traffic(kernel_hash: str, storage: str, schedule):
         return None
     for e in d.get("entries", []):
         if e.get("storage") == storage and list(e.get("schedule", [])) == list(schedule):
-            return e.get("dram_bytes_per_launch")
+            # multi-step entries: one launch runs several steps; the figure is per step
+            return e.get("dram_bytes_per_step", e.get("dram_bytes_per_launch"))
     return None
 
 
@@ -502,7 +522,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload][1], "nodes_per_gpu": nodes, "storage": args.storage,
                        "schedule": {"rows": sched[0], "nodes_per_thread": sched[1],
-                                    "persistent": sched[2] == 2,
+                                    "persistent": sched[2] >= 2, "multi_step": _multistep(case, sched),
                                     "chosen_by": "--schedule" if args.schedule else "autotune"},
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (2 x %d MB population buffers), no flush" %
@@ -511,12 +531,15 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _ncu_traffic(khash, args.storage, sched),
                          "algorithmic_bytes_per_node": bytes_per_node,
-                         "kernel": (("step3d_rows_kernel" if sched[2] == 2 and case.nx in (32, 64, 128, 256)
+                         "kernel": (("step3d_rows_kernel" if sched[2] >= 2 and case.nx in (32, 64, 128, 256)
                                      else "step3d_kernel") if case.lattice == "D3Q39" else
-                                    ("step2d_persistent_kernel" if sched[2] == 2 else "step2d_kernel")) +
-                                   f" ({sched[0]} rows, {sched[1]} nodes per thread)"},
+                                    ("step2d_multistep_kernel" if _multistep(case, sched) else
+                                     "step2d_persistent_kernel" if sched[2] >= 2 else "step2d_kernel")) +
+                                   f" ({sched[0]} rows, {sched[1]} nodes per thread)" +
+                                   (", one launch per up to 1024 steps: achieved and traffic per step"
+                                    if _multistep(case, sched) else "")},
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": _launches(case, sched, args.steps),
             "clocks": clocks,
             "cpu_baseline": cpu,
             "storage_variants": variants,

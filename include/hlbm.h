@@ -145,8 +145,14 @@ long long hlbm_step_count(const hlbm_ctx* ctx);
 /* Schedule of the fused step: tile rows per CTA (2D: 4, 8 or 16; D3Q39: 4
  * or 8; 0 = default 8), nodes per thread (1, or 2 on paired FP32 lanes
  * with 8 or 16 rows; 0 = default 2; D2Q37 only) and persistent CTAs that
- * prefetch their next tile (0 = default off, 1 = off, 2 = on; D2Q37 only).
- * Chosen by the autotuner; results agree to rounding across schedules. */
+ * prefetch their next tile (0 = default off, 1 = off, 2 = on, 3 = on and, on
+ * D2Q37 domains that the 32 x rows tiles cover exactly, one launch for up to
+ * 1024 steps of hlbm_step: a tile of step s starts as soon as the tile rows
+ * around it have completed step s - 1, tracked by per-tile-row counters in
+ * the workspace; where a read region exceeds one tile row, 3 runs as 2).
+ * Chosen by the autotuner among 1 and 2 (3, measured slower on GB300, is
+ * opt-in); results agree to rounding across schedules, and 3 agrees with 2
+ * bit for bit. */
 hlbm_status hlbm_set_tile(hlbm_ctx* ctx, int rows, int nodes_per_thread, int persistent);
 
 /* Waits for all work on the context's stream.  Returns HLBM_ETIMEOUT (and

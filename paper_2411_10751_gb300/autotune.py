@@ -1,7 +1,7 @@
 """Schedule autotuner for the fused step.
 
-A schedule is (tile rows, nodes per thread, persistent CTAs) as accepted by
-hlbm_set_tile.  For a given domain the tuner times each candidate on the
+A schedule is (tile rows, nodes per thread, persistent CTAs: 1 off, 2 on,
+3 multi-step) as accepted by hlbm_set_tile.  For a given domain the tuner times each candidate on the
 device with CUDA events (a throwaway context on the same sizes and sources,
 outside any measured region) and keeps the fastest; results are cached per
 GPU, lattice, source kind, storage and size in _build/autotune.json.
@@ -17,6 +17,9 @@ from .solver import HLBM
 
 CACHE = Path(__file__).resolve().parent / "_build" / "autotune.json"
 
+# the multi-step schedule (persistent = 3) is left out: on GB300 it measured
+# slower than one launch per step on every workload tried (its per-tile
+# release and acquire fences cost more than the launch boundary)
 CANDIDATES_2D = [(8, 2, 1), (8, 1, 1), (16, 2, 1), (16, 1, 1), (4, 1, 1), (8, 2, 2), (8, 1, 2)]
 CANDIDATES_3D = [(8, 2, 2), (8, 2, 1), (8, 1, 1), (4, 1, 1)]
 

@@ -30,6 +30,8 @@ struct hlbm_ctx {
   int rows = 8;
   int npt = 2;
   int persistent = 0;
+  bool multistep = false;         // D2Q37: one persistent launch for many steps (tile-row counters)
+  unsigned gen = 0;               // multi-step kernel: steps run since the counters were zeroed
 
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -69,6 +71,9 @@ struct hlbm_ctx {
   int* status = nullptr;          // device status word (bounded waits)
   unsigned long long* tile_ctr = nullptr;  // persistent step's tile counter
   unsigned long long* adj_ctr = nullptr;   // whole-row reverse step's tile counter
+  unsigned long long* ms_ctr = nullptr;    // multi-step kernel's tile counter (zeroed per launch)
+  unsigned* flags = nullptr;               // multi-step kernel: per-tile-row completion counters
+  size_t nflags = 0;
   bool ctr_reset = true;          // the counter must be zeroed before the next step
   unsigned long long wait_ns = 2000000000ull;
   int debug_skip_tma = 0;
@@ -79,7 +84,7 @@ static const int kGraphSteps = 32;  // even: a replay returns to the same buffer
 namespace {
 
 struct Layout {
-  size_t pop_bytes, off_pop1, off_g, off_part, off_red, total;
+  size_t pop_bytes, off_pop1, off_g, off_part, off_red, off_flags, nflags, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -95,7 +100,10 @@ Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) 
   const size_t gbytes = (p->flags & HLBM_SRC_FORCE) ? align256((size_t)D * (size_t)N * 4) : 0;
   L.off_part = L.off_g + gbytes;
   L.off_red = L.off_part + align256((size_t)moment_blocks(lattice, nx, ny, nz) * 8 * sizeof(double));
-  L.total = L.off_red + 256;
+  L.off_flags = L.off_red + 256;
+  // D2Q37: one completion counter per tile row of the smallest tiles (4 rows)
+  L.nflags = (lattice == 0) ? (size_t)((ny + 3) / 4) : 0;
+  L.total = L.off_flags + align256(L.nflags * 4);
   return L;
 }
 
@@ -190,6 +198,9 @@ void carve(hlbm_ctx* c) {
   c->status = reinterpret_cast<int*>(c->arena + L.off_red + 64);
   c->tile_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 128);
   c->adj_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 192);
+  c->ms_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 224);
+  c->flags = L.nflags ? reinterpret_cast<unsigned*>(c->arena + L.off_flags) : nullptr;
+  c->nflags = L.nflags;
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -344,6 +355,54 @@ cudaError_t one_step(hlbm_ctx* c) {
   return e;
 }
 
+// Whether hlbm_step runs the multi-step kernel: D2Q37, tiles that cover the
+// domain exactly, and a read region (pull 3 + neighbour frame H) within one
+// tile row of the tile.
+bool multistep_ok(const hlbm_ctx* c) {
+  if (!c->multistep || c->lattice != HLBM_D2Q37 || !c->flags) return false;
+  const int H = c->kind == KIND_SC ? 3 : (c->kind == KIND_THERMAL ? 1 : 0);
+  return c->nx % 32 == 0 && c->ny % c->rows == 0 && H + 3 <= c->rows;
+}
+
+// Steps of one multi-step launch (tile indices stay below 2^31).
+int multistep_max(const hlbm_ctx* c) {
+  const long long T = (long long)(c->nx / 32) * (c->ny / c->rows);
+  return (int)std::max(1LL, std::min(1024LL, 0x7fffffffLL / T));
+}
+
+// One multi-step launch of S steps from the current buffer.
+cudaError_t launch_multistep(hlbm_ctx* c, int S) {
+  StepArgs a = make_args(c);
+  a.fin = c->pop[c->cur];
+  a.fout = c->pop[c->cur ^ 1];
+  a.msteps = S;
+  a.gen0 = c->gen;
+  a.flags = c->flags;
+  a.ms_ctr = c->ms_ctr;
+  a.tma_store = 0;
+  CUtensorMap maps[2];
+  std::memset(maps, 0, sizeof(maps));
+  if (a.tma) {
+    int wb = 0, hb = 0, ob = 0;
+    step_box_d2q37(c->kind, c->storage, false, c->rows, &wb, &hb, &ob);
+    const CUtensorMap* m0 = tensor_map_at(c, a.fin, wb, hb);
+    const CUtensorMap* m1 = tensor_map_at(c, a.fout, wb, hb);
+    if (m0 && m1) {
+      maps[0] = *m0;
+      maps[1] = *m1;
+    } else {
+      a.tma = 0;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(c->ms_ctr, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = launch_step_d2q37(a, c->kind, c->storage, false, c->rows, c->npt, maps, c->stream);
+  if (e != cudaSuccess) return e;
+  c->gen += (unsigned)S;
+  c->cur ^= (S & 1);
+  c->steps += S;
+  return cudaSuccess;
+}
+
 hlbm_status usable(hlbm_ctx* c) {
   if (!c) return HLBM_EINVAL;
   if (c->failed) return HLBM_ESTATE;
@@ -485,11 +544,13 @@ hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float
   }
   cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess && c->flags) e = cudaMemsetAsync(c->flags, 0, c->nflags * 4, c->stream);
   if (e == cudaSuccess) e = launch_init(c->lattice, a, c->storage, c->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);  // host buffers are borrowed
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   c->cur = 0;
   c->steps = 0;
+  c->gen = 0;
   c->initialised = true;
   c->failed = false;
   return HLBM_OK;
@@ -526,6 +587,14 @@ hlbm_status hlbm_step(hlbm_ctx* c, int n) {
     // the persistent launch's CTA count may have changed: restart the counter
     HLBM_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
     c->ctr_reset = false;
+  }
+  if (multistep_ok(c)) {
+    while (n > 0) {
+      const int S = std::min(n, multistep_max(c));
+      HLBM_CUDA(c, launch_multistep(c, S), "multi-step kernel");
+      n -= S;
+    }
+    return HLBM_OK;
   }
   while (n >= kGraphSteps) {
     cudaGraphExec_t& ge = c->graph[c->cur];
@@ -653,8 +722,10 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
                                cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
+  if (c->flags) HLBM_CUDA(c, cudaMemsetAsync(c->flags, 0, c->nflags * 4, c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   c->cur = 0;
+  c->gen = 0;
   c->steps = hdr[6];
   c->initialised = true;
   return HLBM_OK;
@@ -664,7 +735,8 @@ long long hlbm_step_count(const hlbm_ctx* c) { return c ? c->steps : -1; }
 
 hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread, int persistent) {
   if (!c) return HLBM_EINVAL;
-  if (persistent < 0 || persistent > 2) return fail(c, HLBM_EINVAL, "persistent must be 0 (default off), 1 (off) or 2 (on)");
+  if (persistent < 0 || persistent > 3)
+    return fail(c, HLBM_EINVAL, "persistent must be 0 (default off), 1 (off), 2 (on) or 3 (multi-step)");
   if (rows == 0) rows = 8;
   if (nodes_per_thread == 0) nodes_per_thread = 2;
   if (rows != 4 && rows != 8 && rows != 16) return fail(c, HLBM_EINVAL, "rows must be 4, 8 or 16");
@@ -673,7 +745,8 @@ hlbm_status hlbm_set_tile(hlbm_ctx* c, int rows, int nodes_per_thread, int persi
   if (c->lattice == 1 && rows == 16) return fail(c, HLBM_EINVAL, "D3Q39 tiles have 4 or 8 rows");
   c->rows = rows;
   c->npt = nodes_per_thread;
-  c->persistent = (persistent == 2) ? 1 : 0;
+  c->persistent = (persistent >= 2) ? 1 : 0;
+  c->multistep = persistent == 3 && c->lattice == HLBM_D2Q37;
   c->ctr_reset = true;
   drop_graphs(c);
   return HLBM_OK;

@@ -62,10 +62,10 @@ __device__ __forceinline__ void batch_tile(const BatchDomain& dom, const StepArg
       return;
     }
   } else {
-    fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
+    fill_tile_wrapped<Cf, NT>(a, a.fin, sp, x0, y0, tid);
     __syncthreads();
   }
-  process_tile<ST, KIND, false, kRows, kind_npt<KIND>(), false>(a, nullptr, smem, x0, y0, [] {});
+  process_tile<ST, KIND, false, kRows, kind_npt<KIND>(), false>(a, nullptr, smem, x0, y0, a.fout, [] {});
 }
 
 // Tiles base .. base + gridDim.x - 1 of the work list, all of kind KIND.

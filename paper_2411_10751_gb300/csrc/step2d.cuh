@@ -136,19 +136,21 @@ __device__ __forceinline__ bool tile_boxed(const StepArgs& a, int x0, int y0) {
          (y0 - H + 3 + Cf::HB <= a.ny);
 }
 
-// Edge tile: every region node gathers its Q pulled populations with periodic
-// wrap (independent loads) and writes them into the staged layout.
-template <class Cf, int NT>
-__device__ __forceinline__ void fill_tile_wrapped(const StepArgs& a, typename Cf::T* sp, int x0, int y0, int tid) {
+// Edge tile: every region node gathers its Q pulled populations of `fin_v`
+// with periodic wrap (independent loads through codec C) and writes them into
+// the staged layout.
+template <class Cf, int NT, class C = typename Cf::C>
+__device__ __forceinline__ void fill_tile_wrapped(const StepArgs& a, const void* fin_v, typename Cf::T* sp, int x0,
+                                                  int y0, int tid) {
   using L = D2Q37;
   using T = typename Cf::T;
   constexpr int H = Cf::H;
-  const T* __restrict__ fin = static_cast<const T*>(a.fin);
+  const T* __restrict__ fin = static_cast<const T*>(fin_v);
   for (int k = tid; k < Cf::RW * Cf::RH; k += NT) {
     const int ry = k / Cf::RW, rx = k - ry * Cf::RW;
     const int X = wrapm(x0 - H + rx, a.nx), Y = wrapm(y0 - H + ry, a.ny);
     float gk[37];
-    gather<L, typename Cf::C>(fin, a.N, a.nx, a.ny, 1, X, Y, 0, gk);
+    gather<L, C>(fin, a.N, a.nx, a.ny, 1, X, Y, 0, gk);
     const int base = ry * Cf::WB + rx;
     static_for<37>([&](auto I) {
       constexpr int i = I;
@@ -158,12 +160,13 @@ __device__ __forceinline__ void fill_tile_wrapped(const StepArgs& a, typename Cf
 }
 
 // The work on one staged tile: moments, neighbour fields, sources, collision
-// and stores.  `staged_done()` runs once every read of the staging buffer has
-// finished (after a CTA barrier), so a caller may start refilling it then.
-// TMA_STORE: results leave through the staging buffer by bulk tensor stores.
+// and stores (into fout_v).  `staged_done()` runs once every read of the
+// staging buffer has finished (after a CTA barrier), so a caller may start
+// refilling it then.  TMA_STORE: results leave through the staging buffer by
+// bulk tensor stores.
 template <int ST, int KIND, bool MOM, int BY, int NPT, bool TMA_STORE, class Done>
 __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMap* tmap_out, unsigned char* smem,
-                                             int x0, int y0, Done&& staged_done) {
+                                             int x0, int y0, void* fout_v, Done&& staged_done) {
   using Cf = Cfg2<ST, KIND, MOM, BY>;
   using L = D2Q37;
   using T = typename Cf::T;
@@ -378,7 +381,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
 #pragma unroll
       for (int k = 0; k < NPT; ++k) {
         if (!activek[k]) continue;
-        T* __restrict__ fout = static_cast<T*>(a.fout) + nodek[k];
+        T* __restrict__ fout = static_cast<T*>(fout_v) + nodek[k];
         static_for<37>([&](auto I) {
           constexpr int i = I;
           Cf::C::st(fout + (size_t)i * (size_t)a.N, lane(g[i], k));
@@ -417,10 +420,10 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
       return;
     }
   } else {
-    fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
+    fill_tile_wrapped<Cf, NT>(a, a.fin, sp, x0, y0, tid);
     __syncthreads();
   }
-  process_tile<ST, KIND, MOM, BY, NPT, true>(a, &tmap_out, smem, x0, y0, [] {});
+  process_tile<ST, KIND, MOM, BY, NPT, true>(a, &tmap_out, smem, x0, y0, a.fout, [] {});
 }
 
 // Tiles whose staging boxes lie inside the domain form a rectangle of tile
@@ -546,14 +549,178 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       }
       phase ^= 1u;
     } else {
-      fill_tile_wrapped<Cf, NT>(a, sp, x0, y0, tid);
+      fill_tile_wrapped<Cf, NT>(a, a.fin, sp, x0, y0, tid);
       __syncthreads();
     }
-    process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, [&] {
+    process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, a.fout, [&] {
       if (tid == 0) take_and_issue();
     });
     __syncthreads();  // s_next is published; the shared aux tile is reused by the next tile
     t = s_next;
+  }
+}
+
+// Multi-step persistent D2Q37 step: one launch runs a.msteps steps of Eq. 4.4
+// on a domain that the 32 x BY tiles cover exactly.  Tiles are taken in the
+// order (step, tile row, tile column) from the launch's counter; the tile of
+// step s reads the output of step s - 1 over its own region and the tiles
+// around it (periodic), and overwrites the buffer that they read in step
+// s - 1, so it starts once tile rows ty - 1, ty and ty + 1 have completed
+// step s - 1.  Each tile row has a completion counter (tiles of that row
+// finished, over all steps since the counters were zeroed): a row has
+// completed step s - 1 when its counter reaches (gen0 + s) ntx, since no tile
+// of a row can finish step s before the row has finished step s - 1.  Every
+// wait points at tiles taken earlier, which running CTAs hold, so the launch
+// needs no co-residency and no grid barrier: the ramp-up and tail of a launch
+// per step are gone, and at a step boundary only the first tile row waits
+// for the last one.
+// Thread 0 keeps the synchronisation off the critical path: it takes tile
+// indices one tile ahead and loads the three counters of a taken tile while
+// the CTA works on the current one; at staged_done a single fence serves as
+// the acquire for the next tile's counters and the release of the CTA's
+// previous tile (its stores have drained by then), then the next tile's
+// copies are issued.  A tile whose rows are not ready yet is waited for after
+// the current tile's stores.  Waits are bounded by a.wait_ns; an expired wait
+// or another CTA's error stops the CTA.
+template <int ST, int KIND, int BY, int NPT>
+__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY, NPT>()))
+    step2d_multistep_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tm_even,
+                            const __grid_constant__ CUtensorMap tm_odd) {
+  using Cf = Cfg2<ST, KIND, false, BY>;
+  constexpr int NT = 32 * BY / NPT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_next, s_ready, s_ok;
+  typename Cf::T* sp = reinterpret_cast<typename Cf::T*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Cf::POP_BYTES + Cf::AUX_BYTES + Cf::RED_BYTES);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const bool aligned = (smem_u32(smem) & 127u) == 0;
+  const int ntx = a.nx / 32, nty = a.ny / BY;
+  const int T = ntx * nty;
+  const int total = T * a.msteps;
+  unsigned* rowcnt = a.flags;
+  auto decode = [&](int v, int& s, int& tx, int& ty) {
+    s = v / T;
+    const int t = v - s * T;
+    ty = t / ntx;
+    tx = t - ty * ntx;
+  };
+  // tid 0 state: the next tile and the counters of its rows (loaded when it
+  // was taken), and the finished tile row whose completion is not released yet
+  int nxt = -1, pend_row = -1;
+  unsigned c0 = 0, c1 = 0, c2 = 0;
+  auto load_rows = [&](int v) {
+    int s, tx, ty;
+    decode(v, s, tx, ty);
+    if (s == 0) return;
+    c0 = ld_relaxed_gpu(rowcnt + ((ty == 0) ? nty - 1 : ty - 1));
+    c1 = ld_relaxed_gpu(rowcnt + ty);
+    c2 = ld_relaxed_gpu(rowcnt + ((ty + 1 == nty) ? 0 : ty + 1));
+  };
+  auto rows_ready = [&](int v) -> bool {
+    int s, tx, ty;
+    decode(v, s, tx, ty);
+    if (s == 0) return true;
+    const unsigned need = (a.gen0 + (unsigned)s) * (unsigned)ntx;
+    return (int)(c0 - need) >= 0 && (int)(c1 - need) >= 0 && (int)(c2 - need) >= 0;
+  };
+  auto release_pending = [&]() {   // after a fence
+    if (pend_row >= 0) {
+      red_relaxed_add_gpu(rowcnt + pend_row, 1u);
+      pend_row = -1;
+    }
+  };
+  // stages tile v (its rows are ready and acquired)
+  auto issue = [&](int v) {
+    int s, tx, ty;
+    decode(v, s, tx, ty);
+    if (aligned && tile_boxed<Cf>(a, tx * 32, ty * BY)) {
+      fence_proxy_async_global();   // the acquired generic-proxy writes before these bulk reads
+      fence_proxy_async_smem();
+      issue_tile<Cf>(sp, (s & 1) ? &tm_odd : &tm_even, bar, tx * 32, ty * BY, a.debug_skip_tma);
+    }
+  };
+  // tid 0 at staged_done: takes the tile after next, releases the previous
+  // tile, and stages the next tile if its rows are ready
+  auto advance = [&]() {
+    const unsigned long long vv = atomicAdd(a.ms_ctr, 1ull);
+    const int cur = nxt;
+    const bool ok = cur >= 0 && rows_ready(cur);
+    fence_acq_rel_gpu();
+    release_pending();
+    if (ok) issue(cur);
+    s_next = cur;
+    s_ready = ok ? 1 : 0;
+    nxt = vv < (unsigned long long)total ? (int)vv : -1;
+    if (nxt >= 0) load_rows(nxt);
+  };
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    const unsigned long long v0 = atomicAdd(a.ms_ctr, 1ull);
+    nxt = v0 < (unsigned long long)total ? (int)v0 : -1;
+    if (nxt >= 0) load_rows(nxt);
+    advance();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int v = s_next, ready = s_ready;
+  while (v >= 0) {
+    int s, tx, ty;
+    decode(v, s, tx, ty);
+    const int x0 = tx * 32, y0 = ty * BY;
+    const bool boxed = aligned && tile_boxed<Cf>(a, x0, y0);
+    if (!ready) {
+      if (tid == 0) {
+        fence_acq_rel_gpu();
+        release_pending();   // the tile may wait for the one this CTA just finished
+        const unsigned k0 = c0, k1 = c1, k2 = c2;   // the lookahead tile's counters
+        bool ok = false;
+        const uint64_t t0 = global_ns();
+        for (uint32_t k = 0; k < (1u << 30); ++k) {
+          load_rows(v);
+          if (rows_ready(v)) {
+            fence_acq_rel_gpu();
+            ok = true;
+            break;
+          }
+          if (*(volatile int*)a.status != 0 || global_ns() - t0 > a.wait_ns) break;
+          __nanosleep(64);
+        }
+        c0 = k0;
+        c1 = k1;
+        c2 = k2;
+        if (ok) issue(v);
+        else atomicCAS(a.status, 0, (int)5 /* HLBM_ETIMEOUT */);
+        s_ok = ok ? 1 : 0;
+      }
+      __syncthreads();
+      if (!s_ok) return;   // nothing of this tile is in flight
+    }
+    if (boxed) {
+      const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
+        mbar_wait_bounded(bar, phase, a.wait_ns);
+        __syncthreads();
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      fill_tile_wrapped<Cf, NT, CodecCG<ST>>(a, (s & 1) ? a.fout : a.fin, sp, x0, y0, tid);
+      __syncthreads();
+    }
+    process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, (s & 1) ? const_cast<void*>(a.fin) : a.fout,
+                                                  [&] {
+                                                    if (tid == 0) advance();
+                                                  });
+    __syncthreads();   // the tile's stores are issued; s_next and s_ready are published
+    if (tid == 0) pend_row = ty;
+    v = s_next;
+    ready = s_ready;
+  }
+  if (tid == 0) {
+    fence_acq_rel_gpu();
+    release_pending();
   }
 }
 
@@ -573,8 +740,11 @@ cudaError_t configure2() {
   cudaError_t e = cudaFuncSetAttribute(step2d_kernel<ST, KIND, MOM, BY, NPT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<ST, KIND, MOM, BY>::SMEM);
   if (e != cudaSuccess || MOM) return e;
-  return cudaFuncSetAttribute(step2d_persistent_kernel<ST, KIND, BY, NPT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<ST, KIND, false, BY>::SMEM);
+  e = cudaFuncSetAttribute(step2d_persistent_kernel<ST, KIND, BY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           Cfg2<ST, KIND, false, BY>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(step2d_multistep_kernel<ST, KIND, BY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg2<ST, KIND, false, BY>::SMEM);
 }
 
 // CTAs of a persistent launch: the resident CTAs per SM times the SM count.
@@ -592,10 +762,36 @@ int persistent_ctas() {
   return n;
 }
 
+template <int ST, int KIND, int BY, int NPT>
+int multistep_ctas() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_multistep_kernel<ST, KIND, BY, NPT>, 32 * BY / NPT,
+                                                  Cfg2<ST, KIND, false, BY>::SMEM);
+    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return n;
+}
+
 template <int ST, int KIND, bool MOM, int BY, int NPT = 1>
 cudaError_t launch2(const StepArgs& a, const CUtensorMap* tmaps, cudaStream_t s) {
   using Cf = Cfg2<ST, KIND, MOM, BY>;
   if constexpr (!MOM) {
+    if (a.msteps > 0) {
+      // tmaps: the staging maps of fin and fout (same box)
+      const int tiles = (a.nx / 32) * (a.ny / BY) * a.msteps;
+      const int ctas = std::min(tiles, multistep_ctas<ST, KIND, BY, NPT>());
+      CUtensorMap t0{}, t1{};
+      if (tmaps) {
+        t0 = tmaps[0];
+        t1 = tmaps[1];
+      }
+      step2d_multistep_kernel<ST, KIND, BY, NPT><<<ctas, dim3(32, BY / NPT, 1), Cf::SMEM, s>>>(a, t0, t1);
+      return cudaGetLastError();
+    }
     if (a.persistent) {
       const int tiles = ((a.nx + 31) / 32) * ((a.ny + BY - 1) / BY);
       const int ctas = std::min(tiles, persistent_ctas<ST, KIND, BY, NPT>());

@@ -57,6 +57,19 @@ template <> struct Codec<ST_BF16> {
   __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Loads through L2 only (no read-only or L1 path): for buffers that other
+// CTAs of the same launch write (the multi-step kernel's edge tiles).
+template <int S>
+struct CodecCG {
+  using T = typename Codec<S>::T;
+  __device__ static __forceinline__ float ld(const T* p) {
+    if constexpr (S == ST_F32) return __ldcg(p);
+    else if constexpr (S == ST_F16) return __half2float(__ldcg(p));
+    else return __bfloat162float(__ldcg(p));
+  }
+  __device__ static __forceinline__ void st(T* p, float v) { Codec<S>::st(p, v); }
+};
+
 __device__ __forceinline__ float to_float(float v) { return v; }
 __device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }

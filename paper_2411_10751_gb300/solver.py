@@ -149,7 +149,8 @@ class HLBM:
         return int(abi.hlbm_step_count(self.ctx))
 
     def set_tile(self, rows: int, nodes_per_thread: int = 0, persistent: int = 0) -> None:
-        """Schedule: rows per tile, nodes per thread, persistent (0 default, 1 off, 2 on)."""
+        """Schedule: rows per tile, nodes per thread, persistent (0 default, 1 off, 2 on,
+        3 multi-step: one launch for many steps, D2Q37)."""
         self._chk(abi.hlbm_set_tile(self.ctx, int(rows), int(nodes_per_thread), int(persistent)))
 
     def adjoint(self, steps: int, ckpt_every: int = 50):

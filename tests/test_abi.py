@@ -100,7 +100,8 @@ def test_create_and_destroy_without_device_work(abi):
     assert b"hlbm_init" in abi.hlbm_last_error(ctx)
     assert abi.hlbm_set_tile(ctx, 5, 1, 0) == abi.HLBM_EINVAL
     assert abi.hlbm_set_tile(ctx, 4, 2, 0) == abi.HLBM_EINVAL
-    assert abi.hlbm_set_tile(ctx, 8, 2, 3) == abi.HLBM_EINVAL
+    assert abi.hlbm_set_tile(ctx, 8, 2, 4) == abi.HLBM_EINVAL
+    assert abi.hlbm_set_tile(ctx, 8, 2, 3) == abi.HLBM_OK    # multi-step
     assert abi.hlbm_destroy(ctx) == abi.HLBM_OK
 
 
