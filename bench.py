@@ -361,11 +361,12 @@ def batched_extra(lrank, ws=1, rank=0, steps=100):
     _barrier(ws)
     ms = _max_over_ranks(ws, e0.elapsed_time(e1))
     nodes = sum(c.nodes for c in all_cases)
+    kinds = {("sc" if c.params.get("SC") else "thermal" if c.params.get("H") else "local") for c in cases}
     b.close()
     for g in ctxs:
         g.close()
     return {"workload": "256 periodic D2Q37 domains (Kolmogorov + H_i, vdW droplets), sides 32..256, FP32",
-            "nodes": nodes, "steps": steps, "launches_per_rank": steps, "ranks": ws,
+            "nodes": nodes, "steps": steps, "launches_per_rank": steps * len(kinds), "ranks": ws,
             "MLUPS": nodes * steps / (ms * 1e-3) / 1e6, "achieved_GBs": 296 * nodes / (ms * 1e-3 / steps) / 1e9}
 
 
@@ -437,6 +438,8 @@ def main():
                     help="device-timed steps only (no e2e, variants, extras or CPU baseline; for profiling)")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="run the adjoint extra alone and print its line (for profiling)")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run the batched extra alone and print its line (for profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="T of the adjoint line")
     ap.add_argument("--adjoint-ckpt", type=int, default=50, help="checkpoint interval of the adjoint line")
     args = ap.parse_args()
@@ -458,6 +461,12 @@ def main():
         pkg.build()
     _barrier(ws)
     pkg.load()
+    if args.only_batched:
+        if rank == 0 or ws > 1:
+            line = batched_extra(lrank, ws, rank)
+            if rank == 0:
+                print(json.dumps({"batched": line}))
+        return 0
     if args.only_adjoint:
         if rank == 0:
             print(json.dumps({"adjoint": adjoint_extra(lrank, steps=args.adjoint_steps, ckpt=args.adjoint_ckpt)}))
