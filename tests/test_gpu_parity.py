@@ -197,6 +197,24 @@ def test_reduced_precision_storage(HLBM, storage, tol_u):
     assert eu < tol_u, (storage, er, eu, et)
 
 
+@pytest.mark.parametrize("storage,nx", [("f16", 32), ("f16", 64), ("bf16", 64)])
+def test_d3q39_reduced_precision_rows(HLBM, storage, nx):
+    """16-bit storage on D3Q39: at nx = 32 a stored row is 64 bytes and the
+    step runs the grid kernel; at nx = 64 the persistent whole-row kernel,
+    with the y-edge planes copied row by row (ny = 19 is not a multiple of
+    the 4-row tiles).  Against the FP64 oracle within the storage bars."""
+    c = W.taylor_green_3d(n=64, tau_hat=0.7, Ma=0.2)
+    sl = (slice(0, 13), slice(0, 19), slice(0, nx))
+    c.rho, c.theta = c.rho[sl].copy(), c.theta[sl].copy()
+    c.u = c.u[(slice(None),) + sl].copy()
+    c.nz, c.ny, c.nx = c.rho.shape
+    rng = np.random.default_rng(3)
+    c.gfield = W.fp32(2e-5 * (2 * rng.random((3,) + c.rho.shape) - 1))
+    mg, mo = run_pair(HLBM, c, 30, storage=storage, rows=8, npt=2, persistent=2)
+    er, eu, et = rel_err(mg, mo)
+    assert eu < (1e-3 if storage == "f16" else 2e-2), (storage, er, eu, et)
+
+
 def test_force_profile_equals_full_field_bitwise(HLBM):
     c = W.kolmogorov(64, nx=40, ny=50)
     a, _ = run_pair(HLBM, c, 30, force_kind="field")
