@@ -372,18 +372,25 @@ def batched_extra(lrank, ws=1, rank=0, steps=100):
             "MLUPS": nodes * steps / (ms * 1e-3) / 1e6, "achieved_GBs": 296 * nodes / (ms * 1e-3 / steps) / 1e9}
 
 
-def adjoint_extra(lrank, n=128, steps=400, ckpt=50):
-    """Adjoint of the body-force step on the D3Q39 Taylor-Green case: forward
-    run with checkpoints, recompute and reverse sweep (hlbm_adjoint_run)."""
+def adjoint_extra(lrank, n=128, steps=400, ckpt=None):
+    """Adjoint of the body-force step on the D3Q39 Taylor-Green case
+    (hlbm_adjoint_run).  ckpt None: every state kept in HBM (checkpoint
+    interval 1: no copies, no recompute) when the device has room, else a
+    checkpoint every 50 steps with one recomputed segment."""
     import torch
+    from paper_2411_10751_gb300 import abi
     from paper_2411_10751_gb300.solver import HLBM
     c = W.taylor_green_3d(n=n, tau_hat=0.6, Ma=0.3, steps=steps)
     sched = tuned_schedule(c, "f32", lrank)      # forward and recompute steps
     g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, device=lrank)
     g.set_tile(*sched)
     g.set_force_field(c.gfield, "field")
+    if ckpt is None:
+        need = abi.hlbm_adjoint_workspace_bytes(g.ctx, steps, 1)
+        free, _ = torch.cuda.mem_get_info(lrank)
+        ckpt = 1 if need + (8 << 30) < free else 50
     g.init(c.rho, c.u, c.theta)
-    g.adjoint(4, 2)                      # warm-up of every kernel on the path
+    g.adjoint(steps, ckpt)               # warm-up: every kernel, the workspace block, the tensor maps
     g.init(c.rho, c.u, c.theta)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -395,7 +402,9 @@ def adjoint_extra(lrank, n=128, steps=400, ckpt=50):
                         f"checkpoint every {ckpt}",
             "seconds": dt, "ms_per_reverse_step": dt * 1e3 / steps, "forward_schedule": list(sched),
             "MLUPS_reverse": c.nodes * steps / dt / 1e6, "loss": loss,
-            "note": "wall time of hlbm_adjoint_run: forward with checkpoints, segment recompute, reverse steps"}
+            "checkpoint_every": ckpt,
+            "note": "wall time of hlbm_adjoint_run: forward steps (into the kept states, or with checkpoints "
+                    "and a recomputed segment), reverse steps"}
 
 
 def run_reference(args, ws, rank):
@@ -443,7 +452,8 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="run the batched extra alone and print its line (for profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="T of the adjoint line")
-    ap.add_argument("--adjoint-ckpt", type=int, default=50, help="checkpoint interval of the adjoint line")
+    ap.add_argument("--adjoint-ckpt", type=int, default=None,
+                    help="checkpoint interval of the adjoint line (default: 1 when every state fits in HBM, else 50)")
     args = ap.parse_args()
     if args.only_device:
         args.no_variants = args.no_extras = args.no_cpu_baseline = True

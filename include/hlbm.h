@@ -175,8 +175,10 @@ hlbm_status hlbm_destroy(hlbm_ctx* ctx);
  * set by hlbm_set_force_field (kind 1), by the discrete adjoint of the step
  * (reverse streaming and the transposed Jacobian of the collision, Eqs. 2.2,
  * 3.3, 4.4, 4.5) with checkpoint-and-recompute: a checkpoint every
- * `ckpt_every` steps and one segment of recomputed states.  Body-force
- * contexts only (HLBM_EUNSUPPORTED with H_i or F^SC).
+ * `ckpt_every` steps and one segment of recomputed states.  ckpt_every = 1
+ * keeps every state (the forward steps write straight into the workspace:
+ * no checkpoint copies, no recompute; 128^3 D3Q39 FP32 over 400 steps takes
+ * about 131 GB).  Body-force contexts only (HLBM_EUNSUPPORTED with H_i or F^SC).
  *   workspace  caller-owned device memory, 256-byte aligned, of at least
  *              hlbm_adjoint_workspace_bytes(ctx, steps, ckpt_every) bytes
  *              (ceil(steps / ckpt_every) + ckpt_every - 1 states, two FP32

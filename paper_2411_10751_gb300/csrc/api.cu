@@ -815,11 +815,15 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   const int K = std::min(ckpt_every, steps);
   const AdjLayout L = adj_layout(c, steps, K);
   if (bytes < L.total) return fail(c, HLBM_ENOMEM, "adjoint workspace smaller than hlbm_adjoint_workspace_bytes()");
-  // tensor maps of an earlier run's workspace slots are of no further use
-  std::deque<hlbm_ctx::TMap> keep;
-  for (const auto& t : c->tmaps)
-    if (t.base == c->pop[0] || t.base == c->pop[1]) keep.push_back(t);
-  c->tmaps.swap(keep);
+  // a map depends only on (address, box, type, extent), so maps of an earlier
+  // run's workspace stay valid for a workspace at the same address; the cache
+  // is only trimmed back to the context's own buffers when it grows large
+  if (c->tmaps.size() > 8192) {
+    std::deque<hlbm_ctx::TMap> keep;
+    for (const auto& t : c->tmaps)
+      if (t.base == c->pop[0] || t.base == c->pop[1]) keep.push_back(t);
+    c->tmaps.swap(keep);
+  }
   char* ws = static_cast<char*>(workspace);
   auto state = [&](size_t k) { return static_cast<void*>(ws + k * L.state); };
   float* lam[2] = {reinterpret_cast<float*>(ws + L.off_lam0), reinterpret_cast<float*>(ws + L.off_lam1)};
@@ -829,11 +833,28 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   const float rho0 = (float)c->p.rho0, omega = (float)(1.0 / c->tau_hat), beta = (float)(1.0 - 0.5 / c->tau_hat);
   // forward: checkpoint k is the state before step k K (its gather is f_{kK})
   const int nseg = (int)L.nseg;
-  for (int k = 0; k < nseg; ++k) {
-    HLBM_CUDA(c, cudaMemcpyAsync(state(k), c->pop[c->cur], sbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
-    const int len = std::min(K, steps - k * K);
-    for (int j = 0; j < len; ++j) HLBM_CUDA(c, one_step(c), "forward step");
-    c->steps += len;
+  // K = 1 keeps every state: step k reads slot k and writes slot k + 1, slot 0
+  // being the current buffer and slot T the other one (the final state, as
+  // after hlbm_step), so there is neither a checkpoint copy nor a recompute
+  const int cur0 = c->cur;
+  auto slot = [&](int k) -> void* { return k == 0 ? c->pop[cur0] : (k == steps ? c->pop[cur0 ^ 1] : state(k)); };
+  if (K == 1) {
+    for (int k = 0; k < steps; ++k) {
+      StepArgs a = make_args(c);
+      a.fin = slot(k);
+      a.fout = slot(k + 1);
+      HLBM_CUDA(c, launch_step(c, a, false), "forward step");
+    }
+    c->cur = cur0 ^ 1;
+    c->steps += steps;
+  } else {
+    for (int k = 0; k < nseg; ++k) {
+      HLBM_CUDA(c, cudaMemcpyAsync(state(k), c->pop[c->cur], sbytes, cudaMemcpyDeviceToDevice, c->stream),
+                "checkpoint");
+      const int len = std::min(K, steps - k * K);
+      for (int j = 0; j < len; ++j) HLBM_CUDA(c, one_step(c), "forward step");
+      c->steps += len;
+    }
   }
   // seed from the final state: lambda_T, dL/dg at T, kinetic energy
   const AdjRows gather_only{nullptr, c->status, c->wait_ns, nullptr};
@@ -869,7 +890,7 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   for (int k = nseg - 1; k >= 0; --k) {
     const int len = std::min(K, steps - k * K);
     // states of the segment: j = 0 is checkpoint k, j >= 1 are recomputed into slots nseg + j - 1
-    auto seg = [&](int j) { return j == 0 ? state(k) : state((size_t)nseg + j - 1); };
+    auto seg = [&](int j) { return j == 0 ? (K == 1 ? slot(k) : state(k)) : state((size_t)nseg + j - 1); };
     for (int j = 1; j < len; ++j) {
       StepArgs a = make_args(c);   // staged by tensor maps of the workspace slots
       a.fin = seg(j - 1);
