@@ -350,6 +350,7 @@ cudaError_t one_step(hlbm_ctx* c) {
   StepArgs a = make_args(c);
   a.fin = c->pop[c->cur];
   a.fout = c->pop[c->cur ^ 1];
+  a.reverse = c->cur;   // alternate the tile order: each step starts where the previous one ended
   cudaError_t e = launch_step(c, a, false);
   c->cur ^= 1;
   return e;
@@ -843,6 +844,7 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
       StepArgs a = make_args(c);
       a.fin = slot(k);
       a.fout = slot(k + 1);
+      a.reverse = k & 1;
       HLBM_CUDA(c, launch_step(c, a, false), "forward step");
     }
     c->cur = cur0 ^ 1;

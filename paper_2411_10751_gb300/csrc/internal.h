@@ -47,6 +47,7 @@ struct StepArgs {
   unsigned long long* tile_ctr;  // persistent step: tile counter; each launch takes exactly tiles + CTAs values
   unsigned long long wait_ns;  // wall-time limit of a bounded mbarrier wait
   int debug_skip_tma;     // test hook: arm the barrier but issue no copy (the wait must expire)
+  int reverse;            // persistent step: take the tiles in reverse order (set on every other step)
   // multi-step persistent 2D kernel: steps of this launch (step s reads fin
   // for even s, fout for odd s), steps run before it since the counters were
   // zeroed, per-tile-row completion counters and the launch's tile counter

@@ -502,15 +502,19 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
   const int ntiles = ts.ntx * ts.nty;
   const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
   const bool edge_first = ts.ne * 20 > ntiles;
+  // a.reverse (every other step): the row-major part of the order runs
+  // backwards, so a step starts on the tiles the previous step wrote last,
+  // which are still in L2
   auto origin = [&](int t, int& x0, int& y0) {
     int tx, ty;
     if (!edge_first) {
-      ty = t / ts.ntx;
-      tx = t - ty * ts.ntx;
+      const int u = a.reverse ? ntiles - 1 - t : t;
+      ty = u / ts.ntx;
+      tx = u - ty * ts.ntx;
     } else if (t < ts.ne) {
       ts.edge(t, tx, ty);
     } else {
-      ts.interior(t - ts.ne, tx, ty);
+      ts.interior(a.reverse ? ts.ni - 1 - (t - ts.ne) : t - ts.ne, tx, ty);
     }
     x0 = tx * 32;
     y0 = ty * BY;

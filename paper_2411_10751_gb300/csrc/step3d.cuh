@@ -185,8 +185,16 @@ __global__ void __launch_bounds__(128, 3)
   int pcy = 0, pcz = 0;   // this thread's plane (tid < Q) for issuing copies
   if (tid < L::Q) d3_cyz(tid, pcy, pcz, typename make_iseq<L::Q>::type{});
   // threads tid < Q: the copies of plane tid of tile t (the barrier is armed)
+  // tile t's z-plane and first row; a.reverse (every other step) runs the
+  // order backwards, so a step starts on the tiles the previous one wrote last
+  auto tile_of = [&](int t, int& z, int& y0) {
+    const int u = a.reverse ? ntiles - 1 - t : t;
+    z = u / nty;
+    y0 = (u - z * nty) * by;
+  };
   auto issue_plane = [&](int t) {
-    const int z = t / nty, y0 = (t - z * nty) * by;
+    int z, y0;
+    tile_of(t, z, y0);
     const int zz = wrap_near3(z - pcz, nz);
     const int ys = y0 - pcy;
     fence_proxy_async_smem();
@@ -215,7 +223,8 @@ __global__ void __launch_bounds__(128, 3)
   if (t < ntiles && tid < L::Q && !a.debug_skip_tma) issue_plane(t);
   uint32_t phase = 0;
   for (int it = 1; t < ntiles; ++it) {
-    const int z = t / nty, y0 = (t - z * nty) * by;
+    int z, y0;
+    tile_of(t, z, y0);
     const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) atomicExch(a.status, (int)5 /* HLBM_ETIMEOUT */);
