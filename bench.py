@@ -221,7 +221,7 @@ def tuned_schedule(case, storage, lrank):
 
 
 def forward_sweep(lrank, steps=400, warmup=20):
-    """The other forward configurations judged against the HBM roofline: the
+    """The other forward configurations measured against the HBM roofline: the
     Kolmogorov flow at 2048^2 and 4096^2 and the D3Q39 Taylor-Green 128^3 step."""
     peak, kind = _peaks()
     out = []

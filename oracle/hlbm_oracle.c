@@ -33,7 +33,7 @@
  *        f*_i = f^_i - (f^_i - f^eq_i) / tau^ + (1 - 1 / (2 tau^)) S_i
  *   5. streaming: f^_i(x + c_i, t + 1) = f*_i(x), periodic in every axis.
  *
- * Readings of garbled or silent passages (all listed in the design doc):
+ * Readings of garbled or silent passages:
  *   - Table 2, F_i: the last term is -(c.u)(u.F)/c0^4 as in Eq. 3.3; the
  *     printed -(c.u)(c.F)/c0^4 would cancel the second term.
  *   - Table 2, H_i: factor (1 - 1/Pr) as in Eq. 3.7; the printed
