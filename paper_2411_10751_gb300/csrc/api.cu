@@ -306,8 +306,11 @@ const CUtensorMap* tensor_map(hlbm_ctx* c, int buf, int wb, int hb) { return ten
 cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
   if (c->lattice != 0) {
     // persistent whole-row kernel: box of 256 / nx rows, and single rows
-    CUtensorMap maps3[2];
+    // and, with a force field, a box of its three planes
+    CUtensorMap maps3[3];
+    std::memset(maps3, 0, sizeof(maps3));
     const CUtensorMap* tm = nullptr;
+    a.g_staged = 0;
     if (!moments && a.persistent && a.tma && (c->nx == 32 || c->nx == 64 || c->nx == 128 || c->nx == 256)) {
       const CUtensorMap* mb = tensor_map_at(c, a.fin, c->nx, 256 / c->nx);
       const CUtensorMap* mr = tensor_map_at(c, a.fin, c->nx, 1);
@@ -315,6 +318,13 @@ cudaError_t launch_step(hlbm_ctx* c, StepArgs a, bool moments) {
         maps3[0] = *mb;
         maps3[1] = *mr;
         tm = maps3;
+        if (a.force_mode == FORCE_FIELD && c->gfield) {
+          const CUtensorMap* mg = tensor_map_at(c, c->gfield, c->nx, 256 / c->nx, true, 3);
+          if (mg) {
+            maps3[2] = *mg;
+            a.g_staged = 1;
+          }
+        }
       }
     }
     return launch_step_d3q39(a, c->kind, c->storage, moments, c->rows, c->npt, tm, c->stream);

@@ -48,6 +48,7 @@ struct StepArgs {
   unsigned long long wait_ns;  // wall-time limit of a bounded mbarrier wait
   int debug_skip_tma;     // test hook: arm the barrier but issue no copy (the wait must expire)
   int reverse;            // persistent step: take the tiles in reverse order (set on every other step)
+  int g_staged;           // D3Q39 whole-row step: the force field is staged with the tiles (third tensor map)
   // multi-step persistent 2D kernel: steps of this launch (step s reads fin
   // for even s, fout for odd s), steps run before it since the counters were
   // zeroed, per-tile-row completion counters and the launch's tile counter

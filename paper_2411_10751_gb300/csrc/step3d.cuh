@@ -148,15 +148,17 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas3<MOM, NPT>()))
 // thread (tile nodes t and t + 128) on the paired FP32 lanes.
 constexpr int kRows3Nodes = 256;
 
+// population planes, then two slots (by tile parity) of the tile's
+// acceleration (3 FP32 planes, used with a force field), then the mbarrier
 template <int ST>
 constexpr int rows3_smem() {
-  return D3Q39::Q * kRows3Nodes * (int)sizeof(typename Codec<ST>::T) + 16;
+  return D3Q39::Q * kRows3Nodes * (int)sizeof(typename Codec<ST>::T) + 2 * 3 * kRows3Nodes * 4 + 16;
 }
 
 template <int ST>
 __global__ void __launch_bounds__(128, 3)
     step3d_rows_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tm_box,
-                       const __grid_constant__ CUtensorMap tm_row) {
+                       const __grid_constant__ CUtensorMap tm_row, const __grid_constant__ CUtensorMap tm_g) {
   using L = D3Q39;
   using C = Codec<ST>;
   using T = typename C::T;
@@ -168,7 +170,12 @@ __global__ void __launch_bounds__(128, 3)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_next[2];
   T* sp = reinterpret_cast<T*>(smem);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::Q * TN * (int)sizeof(T));
+  float* sg = reinterpret_cast<float*>(smem + L::Q * TN * (int)sizeof(T));   // acceleration [2][3][TN]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::Q * TN * (int)sizeof(T) + 2 * 3 * TN * 4);
+  // a.g_staged: the force field's planes come with the tile (threads Q .. Q + 2 copy them)
+  const bool gs = a.g_staged != 0;
+  const uint32_t tx = TX + (gs ? 3u * TN * 4u : 0u);
+  const int issuers = L::Q + (gs ? 3 : 0);
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int by = TN / nx;
   const int nty = (ny + by - 1) / by;
@@ -192,9 +199,14 @@ __global__ void __launch_bounds__(128, 3)
     z = u / nty;
     y0 = (u - z * nty) * by;
   };
-  auto issue_plane = [&](int t) {
+  auto issue_plane = [&](int t, int slot) {
     int z, y0;
     tile_of(t, z, y0);
+    if (tid >= L::Q) {   // acceleration plane tid - Q into slot `slot`; rows past the y-edge read zero
+      fence_proxy_async_smem();
+      tma_load_4d(sg + (slot * 3 + tid - L::Q) * TN, &tm_g, 0, y0, z, tid - L::Q, bar);
+      return;
+    }
     const int zz = wrap_near3(z - pcz, nz);
     const int ys = y0 - pcy;
     fence_proxy_async_smem();
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(128, 3)
   auto take = [&](int slot) {
     const int t = (int)(atomicAdd(a.tile_ctr, 1ull) % period);
     s_next[slot] = t;
-    if (t < ntiles) mbar_arrive_expect_tx(bar, TX);
+    if (t < ntiles) mbar_arrive_expect_tx(bar, tx);
   };
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -220,7 +232,7 @@ __global__ void __launch_bounds__(128, 3)
   }
   __syncthreads();
   int t = s_next[0];
-  if (t < ntiles && tid < L::Q && !a.debug_skip_tma) issue_plane(t);
+  if (t < ntiles && tid < issuers && !a.debug_skip_tma) issue_plane(t, 0);
   uint32_t phase = 0;
   for (int it = 1; t < ntiles; ++it) {
     int z, y0;
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(128, 3)
     });
     __syncthreads();  // the staging buffer is free and the next index is published
     const int tn = s_next[it & 1];
-    if (tn < ntiles && tid < L::Q && !a.debug_skip_tma) issue_plane(tn);
+    if (tn < ntiles && tid < issuers && !a.debug_skip_tma) issue_plane(tn, it & 1);
 
     int yk[2], nodek[2];
     bool activek[2];
@@ -258,12 +270,20 @@ __global__ void __launch_bounds__(128, 3)
     moments_h<L>(g, dr, acc, J, Pih);
     const V rho = vadd(splat<V>(a.rho0), dr);
     V ga[3];
+    if (gs) {   // this tile's slot; the next tile's copies go to the other one
+      const float* sgc = sg + ((it - 1) & 1) * 3 * TN;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      float gk[3];
-      accel<3>(a, nodek[k], yk[k], gk);
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) set_lane(ga[d], k, gk[d]);
+        for (int k = 0; k < 2; ++k) set_lane(ga[d], k, sgc[d * TN + rk[k] * nx + xk[k]]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        float gk[3];
+        accel<3>(a, nodek[k], yk[k], gk);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) set_lane(ga[d], k, gk[d]);
+      }
     }
     const V F0 = vmul(rho, ga[0]), F1 = vmul(rho, ga[1]), F2 = vmul(rho, ga[2]);
     const V inv_rho = vmap(rho, [](float r) { return 1.f / r; });
@@ -337,7 +357,7 @@ cudaError_t launch_step3d_st(const StepArgs& a, int kind, bool mom, int rows, in
     const int by = kRows3Nodes / a.nx;
     const int tiles = ((a.ny + by - 1) / by) * a.nz;
     const int ctas = std::min(tiles, rows3_ctas<ST>());
-    step3d_rows_kernel<ST><<<ctas, 128, rows3_smem<ST>(), s>>>(a, tmaps[0], tmaps[1]);
+    step3d_rows_kernel<ST><<<ctas, 128, rows3_smem<ST>(), s>>>(a, tmaps[0], tmaps[1], tmaps[2]);
     return cudaGetLastError();
   }
   const int by = (rows == 4) ? 4 : 8;
