@@ -49,6 +49,10 @@ WORKLOADS = {
     "kolmogorov2048": (lambda: W.kolmogorov(2048), "D2Q37 Kolmogorov flow, 2048x2048 periodic, tau=0.8, g=1e-5"),
     "kolmogorov4096": (lambda: W.kolmogorov(4096), "D2Q37 Kolmogorov flow, 4096x4096 periodic, tau=0.8, g=1e-5"),
     "tg3d128": (lambda: W.taylor_green_3d(n=128), "D3Q39 compressible Taylor-Green 128^3, Ma=0.3, tau=0.6, body force"),
+    "thermal2048": (lambda: W.thermal_decay(n=2048), "D2Q37 thermal decay + H_i (Pr=0.71), 2048x2048 periodic, tau=0.7"),
+    "thermal4096": (lambda: W.thermal_decay(n=4096), "D2Q37 thermal decay + H_i (Pr=0.71), 4096x4096 periodic, tau=0.7"),
+    "kolmogorov1024": (lambda: W.kolmogorov(1024), "D2Q37 Kolmogorov flow, 1024x1024 periodic, tau=0.8, g=1e-5"),
+    "tg3d256": (lambda: W.taylor_green_3d(n=256), "D3Q39 compressible Taylor-Green 256^3, Ma=0.3, tau=0.6, body force"),
     "droplet512": (lambda: W.droplet(n=512), "D2Q37 vdW droplet 512x512 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8"),
     "droplet1024": (lambda: W.droplet(n=1024), "D2Q37 vdW droplet 1024x1024 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8"),
 }
