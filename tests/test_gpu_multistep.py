@@ -110,3 +110,24 @@ def test_multistep_falls_back_on_ragged_domains(HLBM):
     ref, _ = _run(HLBM, c, (8, 2, 2), [30])
     got, _ = _run(HLBM, c, (8, 2, 3), [30])
     assert got == ref
+
+
+@pytest.mark.parametrize("lattice", ["D2Q37", "D3Q39"])
+def test_persistent_equals_one_cta_per_tile(HLBM, lattice):
+    """The persistent kernels (prefetch, tile order reversed every other step,
+    D3Q39: whole-row tiles with the force field staged by TMA) run the same
+    per-node arithmetic as the one-CTA-per-tile kernels: bit-identical states
+    after an odd number of steps."""
+    if lattice == "D2Q37":
+        c = _case("thermal", 128, 96)
+    else:
+        c = W.taylor_green_3d(n=64, tau_hat=0.7, Ma=0.2)
+        sl = (slice(0, 13), slice(0, 19), slice(0, 64))
+        c.rho, c.theta = c.rho[sl].copy(), c.theta[sl].copy()
+        c.u = c.u[(slice(None),) + sl].copy()
+        c.nz, c.ny, c.nx = c.rho.shape
+        rng = np.random.default_rng(3)
+        c.gfield = W.fp32(2e-5 * (2 * rng.random((3,) + c.rho.shape) - 1))
+    ref, _ = _run(HLBM, c, (8, 2, 1), [37])
+    got, _ = _run(HLBM, c, (8, 2, 2), [37])
+    assert got == ref
