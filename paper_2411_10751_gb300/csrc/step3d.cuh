@@ -141,11 +141,13 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas3<MOM, NPT>()))
 // population plane of a tile is one 4D tensor box at x = 0 shifted by
 // (-c_y, -c_z), so the periodic wrap in x is an index mask in shared memory
 // and the wrap in z a wrapped box coordinate; a plane whose rows cross the
-// domain's y-edge is copied row by row with wrapped y.  Tiles come in order
-// (y rows, then z planes) from the step's device counter; as soon as a tile's
-// populations are in registers the CTA takes the next index and issues its
-// copies, so the loads overlap the collision and the stores.  Two nodes per
-// thread (tile nodes t and t + 128) on the paired FP32 lanes.
+// domain's y-edge is copied row by row with wrapped y.  With a force field
+// the tile's three acceleration planes come on the same barrier, into one of
+// two slots by tile parity.  Tiles come in order (y rows, then z planes; the
+// order reversed on every other step) from the step's device counter; as soon
+// as a tile's populations are in registers the CTA takes the next index and
+// issues its copies, so the loads overlap the collision and the stores.  Two
+// nodes per thread (tile nodes t and t + 128) on the paired FP32 lanes.
 constexpr int kRows3Nodes = 256;
 
 // population planes, then two slots (by tile parity) of the tile's
@@ -191,7 +193,6 @@ __global__ void __launch_bounds__(128, 3)
   }
   int pcy = 0, pcz = 0;   // this thread's plane (tid < Q) for issuing copies
   if (tid < L::Q) d3_cyz(tid, pcy, pcz, typename make_iseq<L::Q>::type{});
-  // threads tid < Q: the copies of plane tid of tile t (the barrier is armed)
   // tile t's z-plane and first row; a.reverse (every other step) runs the
   // order backwards, so a step starts on the tiles the previous one wrote last
   auto tile_of = [&](int t, int& z, int& y0) {
@@ -199,6 +200,9 @@ __global__ void __launch_bounds__(128, 3)
     z = u / nty;
     y0 = (u - z * nty) * by;
   };
+  // threads tid < Q: the copies of population plane tid of tile t; threads
+  // Q .. Q + 2 (with a staged force field): acceleration plane tid - Q (the
+  // barrier is armed)
   auto issue_plane = [&](int t, int slot) {
     int z, y0;
     tile_of(t, z, y0);
