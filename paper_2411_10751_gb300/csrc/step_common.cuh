@@ -262,8 +262,9 @@ __device__ __forceinline__ V density_h(const V (&g)[L::Q], V& dr_l) {
 // evaluation leaves psi noise of several ulp that F^SC turns into force noise
 // at the interface.  psi^2 is therefore formed in float-float arithmetic
 // (Dekker/Knuth error-free sum and FMA product) from the FP32 density, and
-// the square root takes one Newton correction: psi is within about half an
-// ulp of the value of the formula at the node's density.
+// the square root takes one Newton correction against the float-float
+// residual: psi is within about half an ulp of the value of the formula at
+// the node's density.
 struct ff {
   float h, l;
 };
@@ -286,10 +287,21 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   const float p = __fmul_rn(x.h, y.h);
   return ff_norm(p, fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p))));
 }
+// 1 / y: the hardware approximation refined by one Newton-Raphson step
+// (e = 1 - y r0, r1 = r0 + r0 e); relative error about 2^-23 for normal y.
+__device__ __forceinline__ float rcp_nr(float y) {
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(y));
+  return fmaf(r0, fmaf(-y, r0, 1.f), r0);
+}
+// x / y: a quotient within a few ulp, its exact remainder r = x - q y (error-
+// free product), and the correction r / y; the float-float result does not
+// depend on q being correctly rounded.
 __device__ __forceinline__ ff ff_div(ff x, ff y) {
-  const float q = __fdiv_rn(x.h, y.h);
+  const float inv = rcp_nr(y.h);
+  const float q = __fmul_rn(x.h, inv);
   const ff r = ff_add(x, ff_neg(ff_mul_f(y, q)));
-  return ff_norm(q, __fdiv_rn(r.h, y.h));
+  return ff_norm(q, __fmul_rn(r.h, inv));
 }
 
 // The density enters as rho0 + dr + dr_l, formed exactly as a float-float.
@@ -314,9 +326,14 @@ __device__ __forceinline__ float psi_of(const StepArgs& a, float dr, float dr_l)
   const ff quad = ff_mul(ff_add(ff{2.f, 0.f}, ff_mul(k1, rho)), rho);   // 2 rho + k1 rho^2
   const ff s = ff_add(quad, ff_neg(ff_mul(k2, z)));
   if (!(s.h > 0.f)) return 0.f;
-  const float h = __fsqrt_rn(s.h);
+  // square root of s.h + s.l: y ~ 1/sqrt(s.h) from the hardware, h = s.h y
+  // (relative error about 2^-22), then one Newton step against the float-float
+  // residual (Karp-Markstein): h + (s - h^2) y / 2
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(s.h));
+  const float h = __fmul_rn(s.h, y);
   const float r = __fadd_rn(fmaf(-h, h, s.h), s.l);
-  return fmaf(r, __fdiv_rn(0.5f, h), h);
+  return fmaf(r, 0.5f * y, h);
 }
 
 // ---------------------------------------------------------- body acceleration
