@@ -95,7 +95,7 @@ __device__ __forceinline__ float theta_bar_local(const StepArgs& a, float (&g)[L
   const float rho = a.rho0 + dr;
   float gacc[3];
   accel<2>(a, node, y, gacc);
-  const float inv = 1.f / rho;
+  const float inv = rcp_nr(rho);
   const float ux = fmaf(0.5f * rho, gacc[0], J[0]) * inv;
   const float uy = fmaf(0.5f * rho, gacc[1], J[1]) * inv;
   const float G2 = 2.f * rho * (ux * gacc[0] + uy * gacc[1]);
@@ -258,11 +258,11 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
       const float ps = lane(psi, k), fx = lane(fsx, k), fy = lane(fsy, k);
-      set_lane(sigma, k, (ps > 0.f) ? a.p_coef * (fx * fx + fy * fy) / (ps * ps) : 0.f);
+      set_lane(sigma, k, (ps > 0.f) ? a.p_coef * (fx * fx + fy * fy) * rcp_nr(ps * ps) : 0.f);
     }
   }
 
-  const V inv_rho = vmap(rho, [](float r) { return 1.f / r; });
+  const V inv_rho = vmap(rho, [](float r) { return rcp_nr(r); });
   const V ux = vmul(vfma(splat<V>(0.5f), Fx, J[0]), inv_rho);
   const V uy = vmul(vfma(splat<V>(0.5f), Fy, J[1]), inv_rho);
   const V uu = vfma(ux, ux, vmul(uy, uy));

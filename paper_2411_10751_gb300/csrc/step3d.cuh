@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas3<MOM, NPT>()))
     for (int d = 0; d < 3; ++d) set_lane(ga[d], k, gk[d]);
   }
   const V F0 = vmul(rho, ga[0]), F1 = vmul(rho, ga[1]), F2 = vmul(rho, ga[2]);
-  const V inv_rho = vmap(rho, [](float r) { return 1.f / r; });
+  const V inv_rho = vmap(rho, [](float r) { return rcp_nr(r); });
   const V ux = vmul(vfma(splat<V>(0.5f), F0, J[0]), inv_rho);
   const V uy = vmul(vfma(splat<V>(0.5f), F1, J[1]), inv_rho);
   const V uz = vmul(vfma(splat<V>(0.5f), F2, J[2]), inv_rho);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(128, 3)
       }
     }
     const V F0 = vmul(rho, ga[0]), F1 = vmul(rho, ga[1]), F2 = vmul(rho, ga[2]);
-    const V inv_rho = vmap(rho, [](float r) { return 1.f / r; });
+    const V inv_rho = vmap(rho, [](float r) { return rcp_nr(r); });
     const V ux = vmul(vfma(splat<V>(0.5f), F0, J[0]), inv_rho);
     const V uy = vmul(vfma(splat<V>(0.5f), F1, J[1]), inv_rho);
     const V uz = vmul(vfma(splat<V>(0.5f), F2, J[2]), inv_rho);
