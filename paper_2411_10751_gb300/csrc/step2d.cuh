@@ -519,9 +519,14 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
     x0 = tx * 32;
     y0 = ty * BY;
   };
-  // tid 0: takes the next tile index and, if it is a boxed tile, stages it
-  auto take_and_issue = [&]() {
-    const int tn = (int)(atomicAdd(a.tile_ctr, 1ull) % period);
+  // tid 0 takes tile indices one tile ahead, so that the counter's round
+  // trip is not on the path to the next tile's copies: at staged_done it
+  // stages the index taken during the previous tile and only then takes the
+  // next one.  Once it has taken an index >= T it takes no more, so a launch
+  // still takes exactly T + G values.
+  int nxt = 0;
+  auto take = [&]() { return (int)(atomicAdd(a.tile_ctr, 1ull) % period); };
+  auto stage = [&](int tn) {   // tid 0: publishes tile tn and, if it is a boxed tile, stages it
     s_next = tn;
     if (tn < ntiles) {
       int xn, yn;
@@ -532,10 +537,17 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       }
     }
   };
+  auto take_and_issue = [&]() {
+    const int tn = nxt;
+    stage(tn);
+    if (tn < ntiles) nxt = take();
+  };
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
-    take_and_issue();
+    const int t0 = take();
+    stage(t0);
+    nxt = (t0 < ntiles) ? take() : t0;
   }
   __syncthreads();
   uint32_t phase = 0;
