@@ -103,6 +103,17 @@ def test_reduced_storage_adjoint(HLBM, storage):
     assert err < 5e-2, err
 
 
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_keep_every_state_short_runs(HLBM, steps):
+    """Checkpoint interval 1 keeps every state, with the first and last slots
+    being the context's own buffers: the shortest runs against the oracle."""
+    c = _case3d(n=32, nx=32, ny=11, nz=9)
+    loss, grad = _gpu(HLBM, c, steps, 1)
+    lref, gref = _ref(c, steps)
+    assert abs(loss - lref) < 1e-5 * abs(lref), (loss, lref)
+    assert np.abs(grad - gref).max() / np.abs(gref).max() < 1e-4
+
+
 def test_checkpoint_interval_does_not_change_the_gradient(HLBM):
     c = _case3d()
     res = [_gpu(HLBM, c, 24, K) for K in (1, 5, 24)]

@@ -108,15 +108,17 @@ def test_kolmogorov_schedules(HLBM, rows, npt, pers):
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
+@pytest.mark.parametrize("pers", [1, 2])
 @pytest.mark.parametrize("kind,nx,ny", [("thermal", 8, 12), ("thermal", 36, 20), ("droplet", 32, 32),
                                         ("droplet", 40, 28)])
-def test_domains_narrower_than_a_staged_row(HLBM, kind, nx, ny):
-    """Domains narrower than a staged box row: each row wraps several times."""
+def test_domains_narrower_than_a_staged_row(HLBM, kind, nx, ny, pers):
+    """Domains narrower than a staged box row: each row wraps several times;
+    with persistent CTAs (pers 2) most CTAs draw a stop index at once."""
     if kind == "thermal":
         c = W.thermal_decay(nx=nx, ny=ny, tau_hat=0.7, Pr=0.71)
     else:
         c = W.droplet(nx=nx, ny=ny, r0=0.25 * nx, k=1.5672)
-    mg, mo = run_pair(HLBM, c, 30, rows=8, npt=2)
+    mg, mo = run_pair(HLBM, c, 30, rows=8, npt=2, persistent=pers)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
 
 
