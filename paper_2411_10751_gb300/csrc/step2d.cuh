@@ -511,10 +511,18 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       const int u = a.reverse ? ntiles - 1 - t : t;
       ty = u / ts.ntx;
       tx = u - ty * ts.ntx;
-    } else if (t < ts.ne) {
-      ts.edge(t, tx, ty);
     } else {
-      ts.interior(a.reverse ? ts.ni - 1 - (t - ts.ne) : t - ts.ne, tx, ty);
+      // edge tiles first, except for the pseudopotential kind, where boxed
+      // tiles open and close the step and the gathered edge tiles sit in the
+      // middle (same-box: droplet 1024^2 12.07k -> 12.31k MLUPS; the thermal
+      // step loses 4% that way)
+      const int h = (KIND == KIND_SC) ? ts.ni / 2 : 0;
+      if (t >= h && t < h + ts.ne) {
+        ts.edge(t - h, tx, ty);
+      } else {
+        const int j = t < h ? t : t - ts.ne;
+        ts.interior(a.reverse ? ts.ni - 1 - j : j, tx, ty);
+      }
     }
     x0 = tx * 32;
     y0 = ty * BY;
