@@ -71,7 +71,7 @@ def brute_step(L, p, tau_hat, f, g, shape):
     if p.get("SC"):
         acc = np.zeros((D,) + shape)
         for i in range(Q):
-            acc += L.w[i] * shifted(psi_g, L.c[i])[None] * L.c[i][:, None, None]
+            acc += L.w[i] * shifted(psi_g, L.c[i])[None] * L.c[i].reshape((D,) + (1,) * D)
         Fsc = (-(-1.0) * psi_g[None] * acc).reshape(D, N)
     if g is not None:
         gg = g.reshape(D, N)
