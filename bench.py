@@ -138,18 +138,83 @@ def _ncu_traffic(kernel_hash: str, storage: str, schedule):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clocks and throttle reasons sampled during the timed region.
+
+    A thread reads NVML (libnvidia-ml through ctypes) every few milliseconds
+    while the region runs, plus one sample right before and one right after,
+    so even a region of a few milliseconds has samples; where NVML cannot be
+    loaded, nvidia-smi is polled every 100 ms instead."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_s: float = 0.002):
         self.gpu = gpu_index
+        self.period = period_s
+        self.rows = []            # (sm_mhz, max_mhz, reason bits)
         self.proc = None
         self.path = None
+        self._nvml = None
+        self._h = None
+        self._thread = None
+        self._stop = None
+
+    def _nvml_open(self):
+        import ctypes as C
+        try:
+            lib = C.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if lib.nvmlInit_v2() != 0:
+            return False
+        h = C.c_void_p()
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        ok = -1
+        if ids and self.gpu < len(ids):
+            tok = ids[self.gpu]
+            if tok.isdigit():
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(int(tok), C.byref(h))
+            else:
+                ok = lib.nvmlDeviceGetHandleByUUID(tok.encode(), C.byref(h))
+        else:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(self.gpu, C.byref(h))
+        if ok != 0:
+            return False
+        self._nvml, self._h = lib, h
+        return True
+
+    def sample(self):
+        import ctypes as C
+        if self._nvml is None:
+            return
+        mhz, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        lib = self._nvml
+        if lib.nvmlDeviceGetClockInfo(self._h, 1, C.byref(mhz)) != 0:      # NVML_CLOCK_SM
+            return
+        lib.nvmlDeviceGetMaxClockInfo(self._h, 1, C.byref(mx))
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self._h, C.byref(rs))
+        self.rows.append((float(mhz.value), float(mx.value), int(rs.value)))
+
+    def _loop(self):
+        while not self._stop.is_set():
+            self.sample()
+            self._stop.wait(self.period)
 
     def __enter__(self):
+        import threading
+        if self._nvml_open():
+            self._stop = threading.Event()
+            self.sample()
+            self._thread = threading.Thread(target=self._loop, daemon=True)
+            self._thread.start()
+            return self
         try:
             import tempfile
             fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -162,32 +227,38 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join()
+            self.sample()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            bits = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                    "sw_power_cap": 0x4}
+            if self.path and os.path.exists(self.path):
+                for line in open(self.path):
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        r = sum(bits[names[k]] for k in range(4) if parts[5 + k].lower() == "active")
+                        self.rows.append((float(parts[1]), float(parts[2]), r))
+                    except ValueError:
+                        continue
+                os.unlink(self.path)
 
     def summary(self):
-        if self.proc is None or not self.path or not os.path.exists(self.path):
+        if not self.rows:
             return None
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
-        os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({name for _, _, r in self.rows for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+                "sm_mhz_min": min(r[0] for r in self.rows), "reasons": reasons, "samples": len(self.rows),
+                "source": "nvml" if self._nvml is not None else "nvidia-smi"}
 
 
 def _barrier(ws):
@@ -232,7 +303,7 @@ def forward_sweep(lrank, steps=400, warmup=20):
     for name in ("kolmogorov2048", "kolmogorov4096", "tg3d128"):
         case = WORKLOADS[name][0]()
         sched = tuned_schedule(case, "f32", lrank)
-        ms, _, _ = time_device(case, "f32", steps, warmup, 1, lrank, sched)
+        ms, _, _, _ = time_device(case, "f32", steps, warmup, 1, lrank, sched)
         mlups = case.nodes * steps / (ms * 1e-3) / 1e6
         gbs = _bytes_per_node(case, "f32") * mlups / 1e3
         out.append({"workload": WORKLOADS[name][1], "storage": "f32", "schedule": list(sched), "MLUPS": mlups,
@@ -240,8 +311,15 @@ def forward_sweep(lrank, steps=400, warmup=20):
     return out
 
 
-def time_device(case, storage, steps, warmup, ws, lrank, schedule=None):
-    """Device-resident run: K steps timed with CUDA events on the context's stream."""
+REPEATS = 5
+
+
+def time_device(case, storage, steps, warmup, ws, lrank, schedule=None, repeats=REPEATS):
+    """Device-resident run: W warm-up steps, then `repeats` timed regions of
+    exactly K steps, each bracketed by a barrier and a device synchronize and
+    timed with CUDA events on the context's stream; returns the median region
+    (ms), the clock record over all regions, the FP64 diagnostics and every
+    region's time."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM
     g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage, device=lrank)
@@ -252,26 +330,50 @@ def time_device(case, storage, steps, warmup, ws, lrank, schedule=None):
     g.step(warmup)
     g.synchronize()
     s = g.cuda_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    _barrier(ws)
-    torch.cuda.synchronize()
+    times = []
     with ClockSampler(lrank) as clk:
-        e0.record(s)
-        g.step(steps)
-        e1.record(s)
-        e1.synchronize()
-    torch.cuda.synchronize()
-    _barrier(ws)
-    ms = e0.elapsed_time(e1)
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            _barrier(ws)
+            torch.cuda.synchronize()
+            e0.record(s)
+            g.step(steps)
+            e1.record(s)
+            e1.synchronize()
+            torch.cuda.synchronize()
+            _barrier(ws)
+            times.append(e0.elapsed_time(e1))
     d = g.diag()
     g.close()
-    return ms, clk.summary(), d
+    return statistics.median(times), clk.summary(), d, times
 
 
-def time_e2e(case, storage, steps, ws, lrank, schedule=None):
+def profile_window(case, storage, steps, warmup, lrank, schedule):
+    """K consecutive steps after W warm-up steps, bracketed by cudaProfilerStart /
+    cudaProfilerStop: under an ncu range capture without cache control the
+    window starts in the steady state of the step sequence, so the dirty
+    lines the window inherits balance those it leaves, and its DRAM bytes / K
+    are the traffic of one step."""
+    import torch
+    from paper_2411_10751_gb300.solver import HLBM
+    g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage, device=lrank)
+    g.set_tile(*schedule)
+    _set_force(g, case)
+    g.init(case.rho, case.u, case.theta)
+    g.step(warmup)
+    g.synchronize()
+    torch.cuda.profiler.start()
+    g.step(steps)
+    g.synchronize()
+    torch.cuda.profiler.stop()
+    g.close()
+
+
+def time_e2e(case, storage, steps, ws, lrank, schedule=None, repeats=REPEATS):
     """Through the public API with host buffers: pinned host fields -> hlbm_init
-    (H2D), K steps, hlbm_moments to pinned host buffers (D2H); wall time."""
+    (H2D), K steps, hlbm_moments to pinned host buffers (D2H); wall time, the
+    median of `repeats` runs."""
     import torch
     from paper_2411_10751_gb300.solver import HLBM
     g = HLBM(case.lattice, case.nx, case.ny, case.nz, case.tau_hat, case.params, storage=storage, device=lrank)
@@ -282,60 +384,83 @@ def time_e2e(case, storage, steps, ws, lrank, schedule=None):
     out = {k: torch.empty_like(pin[k]).pin_memory() for k in pin}
     g.init(pin["rho"].numpy(), pin["u"].numpy(), pin["theta"].numpy())   # warm-up of the path
     g.synchronize()
-    _barrier(ws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     from paper_2411_10751_gb300 import abi
-    abi.check(abi.hlbm_init(g.ctx, pin["rho"].data_ptr(), pin["u"].data_ptr(), pin["theta"].data_ptr(), 0), g.ctx)
-    abi.check(abi.hlbm_step(g.ctx, steps), g.ctx)
-    abi.check(abi.hlbm_moments(g.ctx, out["rho"].data_ptr(), out["u"].data_ptr(), out["theta"].data_ptr(), 0), g.ctx)
-    t1 = time.perf_counter()
-    _barrier(ws)
+    times = []
+    for _ in range(repeats):
+        _barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        abi.check(abi.hlbm_init(g.ctx, pin["rho"].data_ptr(), pin["u"].data_ptr(), pin["theta"].data_ptr(), 0),
+                  g.ctx)
+        abi.check(abi.hlbm_step(g.ctx, steps), g.ctx)
+        abi.check(abi.hlbm_moments(g.ctx, out["rho"].data_ptr(), out["u"].data_ptr(), out["theta"].data_ptr(), 0),
+                  g.ctx)
+        t1 = time.perf_counter()
+        _barrier(ws)
+        times.append((t1 - t0) * 1e3)
     h2d = sum(t.numel() * 4 for t in pin.values())
     d2h = sum(t.numel() * 4 for t in out.values())
     assert np.isfinite(out["u"].numpy()).all()
     g.close()
-    return (t1 - t0) * 1e3, h2d, d2h
+    return statistics.median(times), h2d, d2h
 
 
-def storage_errors(n=256, steps=100):
-    """Per-field error of each storage against the FP64 oracle on an n^2 copy of the workload."""
+def storage_errors(case, schedules, steps=100):
+    """Per-field error of each storage against the FP64 oracle on the benchmark
+    workload itself, each storage on the schedule its timing used."""
     from oracle.solver import Oracle
     from paper_2411_10751_gb300.solver import HLBM
-    c = W.thermal_decay(n=n)
-    o = Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
+    c = case
+    o = Oracle(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params)
+    if c.gfield is not None:
+        o.set_force_field(c.gfield)
     o.init(c.rho, c.u, c.theta)
     o.run(steps)
     r0, u0, t0 = o.moments()
     res = {}
-    for st in ("f32", "f16", "bf16"):
-        g = HLBM(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params, storage=st)
+    for st, sched in schedules.items():
+        g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, storage=st)
+        g.set_tile(*sched)
+        _set_force(g, c)
         g.init(c.rho, c.u, c.theta)
         g.step(steps)
         r, u, t = g.moments_host()
         g.close()
         res[st] = {"rho": float(np.abs(r - r0).max() / np.abs(r0).max()),
                    "u": float(np.sqrt(((u - u0) ** 2).sum(0)).max() / np.sqrt((u0 ** 2).sum(0)).max()),
-                   "theta": float(np.abs(t - t0).max() / np.abs(t0).max())}
-    return {"case": f"{n}x{n} copy of the workload, {steps} steps, max|q-q_oracle|/max|q_oracle|", **res}
+                   "theta": float(np.abs(t - t0).max() / np.abs(t0).max()), "schedule": list(sched)}
+    return {"case": f"the benchmark workload ({c.nx}x{c.ny}), {steps} steps, each storage on its timed schedule, "
+                    "max|q-q_oracle|/max|q_oracle|", **res}
 
 
-def cpu_baseline(budget_s=12.0, n=1024):
-    """FP64 oracle on the host cores over the full 1024^2 workload, as many
-    whole steps as fit in about budget_s seconds (at least 2)."""
+def _oracle_mlups(o, nodes, budget_s, min_steps=1):
+    o.run(1)
+    t0 = time.perf_counter()
+    k = 0
+    while k < min_steps or time.perf_counter() - t0 < budget_s:
+        o.run(1)
+        k += 1
+    dt = time.perf_counter() - t0
+    return nodes * k / dt / 1e6, k, dt
+
+
+def cpu_baseline(budget_s=10.0, n=1024):
+    """FP64 oracle on the host cores over the full 1024^2 workload: as many
+    whole steps as fit in about budget_s seconds on all cores (at least 2),
+    and the same with one thread (at least 1 step)."""
     from oracle import solver as osol
     c = W.thermal_decay(n=n)
     o = osol.Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
     o.init(c.rho, c.u, c.theta)
-    o.run(1)
-    t0 = time.perf_counter()
-    k = 0
-    while k < 2 or time.perf_counter() - t0 < budget_s:
-        o.run(1)
-        k += 1
-    dt = time.perf_counter() - t0
-    return {"value": c.nodes * k / dt / 1e6, "unit": METRIC, "cores": osol.get_threads(), "kind": "oracle",
-            "sample": f"{k} FP64 oracle steps of the full {n}x{n} workload ({dt:.1f} s)"}
+    cores = osol.get_threads()
+    v, k, dt = _oracle_mlups(o, c.nodes, budget_s, 2)
+    osol.set_threads(1)
+    v1, k1, dt1 = _oracle_mlups(o, c.nodes, budget_s / 2, 1)
+    osol.set_threads(cores)
+    return {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{k} FP64 oracle steps of the full {n}x{n} workload ({dt:.1f} s) on {cores} threads",
+            "single_thread": {"value": v1, "unit": METRIC, "cores": 1,
+                              "sample": f"{k1} steps of the same workload ({dt1:.1f} s) on one thread"}}
 
 
 def batched_extra(lrank, ws=1, rank=0, steps=100):
@@ -376,23 +501,12 @@ def batched_extra(lrank, ws=1, rank=0, steps=100):
             "MLUPS": nodes * steps / (ms * 1e-3) / 1e6, "achieved_GBs": 296 * nodes / (ms * 1e-3 / steps) / 1e9}
 
 
-def adjoint_extra(lrank, n=128, steps=400, ckpt=None):
-    """Adjoint of the body-force step on the D3Q39 Taylor-Green case
-    (hlbm_adjoint_run).  ckpt None: every state kept in HBM (checkpoint
-    interval 1: no copies, no recompute) when the device has room, else a
-    checkpoint every 50 steps with one recomputed segment."""
+def _adjoint_once(c, sched, lrank, steps, ckpt):
     import torch
-    from paper_2411_10751_gb300 import abi
     from paper_2411_10751_gb300.solver import HLBM
-    c = W.taylor_green_3d(n=n, tau_hat=0.6, Ma=0.3, steps=steps)
-    sched = tuned_schedule(c, "f32", lrank)      # forward and recompute steps
     g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, device=lrank)
     g.set_tile(*sched)
     g.set_force_field(c.gfield, "field")
-    if ckpt is None:
-        need = abi.hlbm_adjoint_workspace_bytes(g.ctx, steps, 1)
-        free, _ = torch.cuda.mem_get_info(lrank)
-        ckpt = 1 if need + (8 << 30) < free else 50
     g.init(c.rho, c.u, c.theta)
     g.adjoint(steps, ckpt)               # warm-up: every kernel, the workspace block, the tensor maps
     g.init(c.rho, c.u, c.theta)
@@ -402,21 +516,56 @@ def adjoint_extra(lrank, n=128, steps=400, ckpt=None):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     g.close()
-    return {"workload": f"D3Q39 Taylor-Green {n}^3, Ma 0.3, tau 0.6: dL/dg of the kinetic energy at step {steps}, "
-                        f"checkpoint every {ckpt}",
-            "seconds": dt, "ms_per_reverse_step": dt * 1e3 / steps, "forward_schedule": list(sched),
-            "MLUPS_reverse": c.nodes * steps / dt / 1e6, "loss": loss,
-            "checkpoint_every": ckpt,
-            "note": "wall time of hlbm_adjoint_run: forward steps (into the kept states, or with checkpoints "
-                    "and a recomputed segment), reverse steps"}
+    del grad
+    torch.cuda.empty_cache()
+    return {"checkpoint_every": ckpt, "seconds": dt, "ms_per_reverse_step": dt * 1e3 / steps,
+            "MLUPS_reverse": c.nodes * steps / dt / 1e6, "loss": loss}
+
+
+def adjoint_extra(lrank, n=128, steps=400, ckpt=None):
+    """Adjoint of the body-force step on the D3Q39 Taylor-Green case
+    (hlbm_adjoint_run), checkpoint every 50 steps (the configuration's
+    interval; ckpt overrides it).  When every state fits in HBM, the same run
+    with interval 1 (no checkpoint copies, no recompute) is reported beside it."""
+    import torch
+    from paper_2411_10751_gb300 import abi
+    from paper_2411_10751_gb300.solver import HLBM
+    c = W.taylor_green_3d(n=n, tau_hat=0.6, Ma=0.3, steps=steps)
+    sched = tuned_schedule(c, "f32", lrank)      # forward and recompute steps
+    main = _adjoint_once(c, sched, lrank, steps, ckpt or 50)
+    out = {"workload": f"D3Q39 Taylor-Green {n}^3, Ma 0.3, tau 0.6: dL/dg of the kinetic energy at step {steps}, "
+                       f"checkpoint every {main['checkpoint_every']}",
+           "forward_schedule": list(sched), **main,
+           "note": "wall time of hlbm_adjoint_run: forward steps with checkpoints, one recomputed segment at a "
+                   "time, reverse steps"}
+    if ckpt is None:
+        g = HLBM(c.lattice, c.nx, c.ny, c.nz, c.tau_hat, c.params, device=lrank)
+        need = abi.hlbm_adjoint_workspace_bytes(g.ctx, steps, 1)
+        g.close()
+        free, _ = torch.cuda.mem_get_info(lrank)
+        if need + (8 << 30) < free:
+            out["every_state_kept"] = _adjoint_once(c, sched, lrank, steps, 1)
+    return out
+
+
+def reference_side(steps: int, rate_mlups: float = 8.0, budget_s: float = 120.0) -> int:
+    """Side of the square sample of the workload the reference arm steps: the
+    full 1024 when (steps + warm-up) oracle steps fit in about budget_s at the
+    oracle's rate, else the largest power of two that does (at least 64)."""
+    n = 1024
+    while n > 64 and steps * n * n / (rate_mlups * 1e6) > budget_s:
+        n //= 2
+    return n
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores,
+    over the benchmark workload (or a bounded square sample of it)."""
     if rank != 0:
         return 0
     from oracle import solver as osol
     osol.build()
-    n = 256
+    n = reference_side(args.steps + args.warmup)
     c = W.thermal_decay(n=n)
     o = osol.Oracle(c.lattice, c.nx, c.ny, 1, c.tau_hat, c.params)
     o.init(c.rho, c.u, c.theta)
@@ -425,12 +574,16 @@ def run_reference(args, ws, rank):
     o.run(args.steps)
     dt = time.perf_counter() - t0
     v = c.nodes * args.steps / dt / 1e6
+    sample = (f"{args.steps} FP64 oracle steps of the full {n}x{n} workload" if n == 1024 else
+              f"{args.steps} FP64 oracle steps on a {n}x{n} sample of the workload (the full 1024x1024 would "
+              f"exceed the time bound at this step count)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}x{n} of the workload"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}x{n}",
+                                            "same_config": n == 1024},
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": osol.get_threads(), "kind": "oracle",
-                             "sample": f"{args.steps} FP64 oracle steps on a {n}x{n} sample of the workload"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -455,6 +608,9 @@ def main():
                     help="run the adjoint extra alone and print its line (for profiling)")
     ap.add_argument("--only-batched", action="store_true",
                     help="run the batched extra alone and print its line (for profiling)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="after the warm-up, run K steps between cudaProfilerStart and cudaProfilerStop and exit "
+                         "(the window an ncu range capture measures)")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="T of the adjoint line")
     ap.add_argument("--adjoint-ckpt", type=int, default=None,
                     help="checkpoint interval of the adjoint line (default: 1 when every state fits in HBM, else 50)")
@@ -489,11 +645,17 @@ def main():
         return 0
 
     case = WORKLOADS[args.workload][0]()
+    if args.profile_range:
+        if rank == 0:
+            sched = tuple(int(v) for v in args.schedule.split(",")) if args.schedule else \
+                tuned_schedule(case, args.storage, lrank)
+            profile_window(case, args.storage, args.steps, args.warmup, lrank, sched)
+        return 0
     if args.schedule:
         sched = tuple(int(v) for v in args.schedule.split(","))
     else:
         sched = tuned_schedule(case, args.storage, lrank)
-    ms, clocks, diag = time_device(case, args.storage, args.steps, args.warmup, ws, lrank, sched)
+    ms, clocks, diag, region_ms = time_device(case, args.storage, args.steps, args.warmup, ws, lrank, sched)
     ms = _max_over_ranks(ws, ms)
     nodes = case.nodes
     value = nodes * args.steps * ws / (ms * 1e-3) / 1e6
@@ -524,18 +686,20 @@ def main():
     if rank == 0:
         if not args.no_variants:
             variants = {}
+            vscheds = {args.storage: sched}
             for st in ("f32", "f16", "bf16"):
                 if st == args.storage:
                     continue
                 k = min(args.steps, 4000)
                 vsched = tuned_schedule(case, st, lrank)
-                vms, _, _ = time_device(case, st, k, args.warmup, 1, lrank, vsched)
+                vms, _, _, _ = time_device(case, st, k, args.warmup, 1, lrank, vsched)
+                vscheds[st] = vsched
                 e = 4 if st == "f32" else 2
                 variants[st] = {"MLUPS": nodes * k / (vms * 1e-3) / 1e6, "schedule": list(vsched),
                                 "achieved_GBs": _bytes_per_node(case, st) * nodes / (vms * 1e-3 / k) / 1e9,
                                 "frac_of_" + peak_kind: _bytes_per_node(case, st) * nodes / (vms * 1e-3 / k) / 1e9 / peak}
             if args.workload == "thermal1024":
-                errors = storage_errors()
+                errors = storage_errors(case, vscheds)
         if not args.no_cpu_baseline:
             cpu = cpu_baseline()
 
@@ -565,6 +729,8 @@ def main():
                                     if _multistep(case, sched) else "")},
             "e2e": e2e,
             "gpu_launches": _launches(case, sched, args.steps),
+            "timing": {"repeats": len(region_ms), "statistic": "median of the timed regions of K steps",
+                       "region_ms": region_ms},
             "clocks": clocks,
             "cpu_baseline": cpu,
             "storage_variants": variants,

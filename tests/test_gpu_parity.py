@@ -123,7 +123,9 @@ def test_domains_narrower_than_a_staged_row(HLBM, kind, nx, ny, pers):
 
 
 def test_thermal_1024_full_size(HLBM):
-    """The benchmark workload at its full size, in the benchmark's launch configuration."""
+    """The benchmark workload at its full size on the default schedule (one CTA
+    per tile); the schedules the benchmark times at this size are checked in
+    test_gpu_fullsize.py."""
     c = W.thermal_decay(n=1024)
     mg, mo = run_pair(HLBM, c, 100)
     assert max(rel_err(mg, mo)) < TOL32, rel_err(mg, mo)
