@@ -32,6 +32,9 @@
  *   4. collision, Eq. 4.4:
  *        f*_i = f^_i - (f^_i - f^eq_i) / tau^ + (1 - 1 / (2 tau^)) S_i
  *   5. streaming: f^_i(x + c_i, t + 1) = f*_i(x), periodic in every axis.
+ *   With walls (Sec. 4.3) the populations that arrive from beyond a wall are
+ *   replaced first (or_wall_complete, Eqs. 4.7-4.8), and grad theta at the
+ *   wall rows is a one-sided second-order difference into the fluid.
  *
  * Readings of garbled or silent passages:
  *   - Table 2, F_i: the last term is -(c.u)(u.F)/c0^4 as in Eq. 3.3; the
@@ -73,6 +76,10 @@ typedef struct {
     int eos;            /* 0: van der Waals, 1: Carnahan-Starling (Eq. 5.9) */
     double eos_a, eos_b, eos_T;
     double k;           /* free parameter of Eq. 3.12 */
+    int walls;          /* 0: periodic in y; 1: TMS walls below and above (Sec. 4.3) */
+    int wall_rule;      /* 0: the reading of Eqs. 4.7-4.8 used; 1: Eq. 4.7 as printed */
+    double wall_u[2][3];     /* velocity of the bottom (0) and top (1) wall */
+    double wall_theta[2];    /* temperature of the bottom and top wall */
 } or_params;
 
 #define G_SC (-1.0)
@@ -230,8 +237,152 @@ void or_macros(const or_lattice* L, const or_params* P, const double* f, const d
     }
 }
 
-/* One step f_in -> f_out (Eq. 4.4 then streaming).  gfield: [D][N] acceleration or NULL. */
-int or_step(const or_lattice* L, const or_params* P, const double* f_in, double* f_out, const double* gfield) {
+/* Tamm-Mott-Smith wall boundary (Sec. 4.3, Eqs. 4.7-4.8): walls below row 0
+ * and above row ny - 1, periodic in x (and z).
+ *
+ * Geometry: rows 0 and ny - 1 are the wall nodes; the solid-liquid interface
+ * lies half a cell inside them, at y = 1/2 and y = ny - 3/2, so the fluid
+ * layer is H = ny - 2 high (Sec. 5.1: 56 rows, "actual height 54"; Sec. 5.3:
+ * 102 rows, H = 100).
+ *
+ * After streaming, a node whose pull source x - c_i lies beyond the wall rows
+ * has an unknown population i: the wall rows and the two rows next to each
+ * (reach 3).  The periodic push of the step delivered there, in the slot of
+ * the opposite direction ibar, the population f*_ibar(x) that left x across
+ * the wall; this routine reads it and replaces the unknowns.
+ *
+ * wall_rule 0 (the reading used), at a node r rows from its wall node:
+ *   f_i = f*_ibar(x) + s f^eq_i(rho_p, u_i, theta_i) - f^eq_ibar(rho_p, u_p, theta_p)
+ * Eq. 4.7 with f_ibar the population that left x in the opposite direction
+ * and the local state (rho_p, u_p, theta_p) the node's moments of the
+ * previous step (the state that population relaxed toward): it comes back
+ * with its non-equilibrium part, its equilibrium exchanged for one at the
+ * wall's state.  u_i, theta_i: the wall's velocity and temperature
+ * extrapolated linearly from the interface, through the first fluid row's
+ * previous moments u_1, theta_1, to the point where population i turned back,
+ * y = r - |c_iy| / 2 rows from the wall node.  s rescales the target density
+ * so that the unknowns carry exactly the mass that left (sum_U f_i =
+ * sum_U f*_ibar): the wall is impermeable.
+ *
+ * wall_rule 1 is Eqs. 4.7-4.8 as printed: the local moments are those of the
+ * mixture of the known populations and f^eq_i(targets) for the unknowns
+ * (Eq. 4.8, with the half-force shift), the targets are the wall's velocity
+ * and temperature at the wall node and the previous moments at the fluid
+ * nodes, and f_i = f_ibar + f^eq_i(target) - f^eq_i(local) with f_ibar the
+ * post-streaming opposite population at x.  It carries almost none of a
+ * moving wall's momentum into the fluid.
+ * bcm holds the previous step's moments [rho, u_1..u_D, theta][N].
+ */
+static int or_opposite(const or_lattice* L, int i) {
+    for (int j = 0; j < L->Q; ++j) {
+        int same = 1;
+        for (int a = 0; a < 3; ++a) same &= (L->c[j][a] == -L->c[i][a]);
+        if (same) return j;
+    }
+    return -1;
+}
+
+/* Eqs. 4.7-4.8 as printed (wall_rule 1) at node n with unknown set unk. */
+static void or_wall_printed(const or_lattice* L, const or_params* P, const double* f, double* fc,
+                            const double* gfield, const double* bcm, long n, long r, int side,
+                            const int* unk, const int* opp) {
+    const long N = (long)P->nx * P->ny * P->nz;
+    const int D = L->D, Q = L->Q;
+    double rt = bcm[n], ut[3] = {0, 0, 0}, tt = bcm[(long)(1 + D) * N + n];
+    for (int a = 0; a < D; ++a) ut[a] = bcm[(long)(1 + a) * N + n];
+    if (r == 0) {
+        for (int a = 0; a < D; ++a) ut[a] = P->wall_u[side][a];
+        tt = P->wall_theta[side];
+    }
+    double feq_t[OR_MAXQ], feq_l[OR_MAXQ];
+    or_feq(L, P->feq_order, rt, ut, P->thermal ? tt : 1.0, feq_t);
+    double rl = 0.0, j[3] = {0, 0, 0}, e = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        const double gi = unk[i] ? feq_t[i] : f[(long)i * N + n];
+        double cc = 0.0;
+        rl += gi;
+        for (int a = 0; a < D; ++a) { j[a] += L->c[i][a] * gi; cc += (double)L->c[i][a] * L->c[i][a]; }
+        e += cc * gi;
+    }
+    double ul[3] = {0, 0, 0}, uu = 0.0, uF = 0.0;
+    for (int a = 0; a < D; ++a) {
+        double ga = 0.0;
+        if (P->use_force) ga = gfield ? gfield[(long)a * N + n] : P->g_uniform[a];
+        const double Fa = rl * ga;
+        ul[a] = (j[a] + 0.5 * Fa) / rl;
+        uu += ul[a] * ul[a];
+        uF += ul[a] * Fa;
+    }
+    const double tl = (e - rl * uu + uF) / (rl * D * L->cs2);
+    or_feq(L, P->feq_order, rl, ul, P->thermal ? tl : 1.0, feq_l);
+    for (int i = 0; i < Q; ++i)
+        if (unk[i]) fc[(long)i * N + n] = f[(long)opp[i] * N + n] + feq_t[i] - feq_l[i];
+}
+
+void or_wall_complete(const or_lattice* L, const or_params* P, const double* f, double* fc,
+                      const double* gfield, const double* bcm) {
+    const long N = (long)P->nx * P->ny * P->nz;
+    const long nx = P->nx, ny = P->ny;
+    const int D = L->D, Q = L->Q;
+    memcpy(fc, f, sizeof(double) * (size_t)Q * N);
+    if (!P->walls) return;
+    int opp[OR_MAXQ];
+    for (int i = 0; i < Q; ++i) opp[i] = or_opposite(L, i);
+    #pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+        const long y = (n / nx) % ny;
+        const int side = (y < ny / 2) ? 0 : 1;
+        const long r = side == 0 ? y : ny - 1 - y;             /* rows from the wall node */
+        int unk[OR_MAXQ], nu = 0;
+        for (int i = 0; i < Q; ++i) {
+            const long ys = y - L->c[i][1];
+            unk[i] = (ys < 0 || ys >= ny);
+            nu += unk[i];
+        }
+        if (!nu) continue;
+        if (P->wall_rule == 1) {
+            or_wall_printed(L, P, f, fc, gfield, bcm, n, r, side, unk, opp);
+            continue;
+        }
+        /* previous moments of this node and of the first fluid row of its column */
+        const long n1 = (n % nx) + nx * ((side == 0 ? 1 : ny - 2) + ny * (n / (nx * ny)));
+        double up[3] = {0, 0, 0}, u1[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) {
+            up[a] = bcm[(long)(1 + a) * N + n];
+            u1[a] = bcm[(long)(1 + a) * N + n1];
+        }
+        const double rp = bcm[n], tp = bcm[(long)(1 + D) * N + n], t1 = bcm[(long)(1 + D) * N + n1];
+        const double* uw = P->wall_u[side];
+        const double tw = P->wall_theta[side];
+        double feq_p[OR_MAXQ];
+        or_feq(L, P->feq_order, rp, up, P->thermal ? tp : 1.0, feq_p);
+        double dep[OR_MAXQ], fw[OR_MAXQ], m_dep = 0.0, m_neq = 0.0, m_w = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            if (!unk[i]) continue;
+            const double turn = (double)r - 0.5 * fabs((double)L->c[i][1]);  /* turning point */
+            const double wgt = (0.5 - turn) / 0.5;                           /* 0 at the interface */
+            double ui[3] = {0, 0, 0}, fe[OR_MAXQ];
+            for (int a = 0; a < D; ++a) ui[a] = uw[a] + wgt * (uw[a] - u1[a]);
+            const double ti = tw + wgt * (tw - t1);
+            or_feq(L, P->feq_order, rp, ui, P->thermal ? ti : 1.0, fe);
+            fw[i] = fe[i];
+            const int mc[3] = {-L->c[i][0], -L->c[i][1], -L->c[i][2]};
+            dep[i] = f[(long)opp[i] * N + nbr(P, n, mc)];      /* f*_ibar(x), pushed to x - c_i */
+            m_dep += dep[i];
+            m_neq += dep[i] - feq_p[opp[i]];
+            m_w += fw[i];
+        }
+        const double s = (m_dep - m_neq) / m_w;             /* sum_U f_i = sum_U f*_ibar */
+        for (int i = 0; i < Q; ++i)
+            if (unk[i]) fc[(long)i * N + n] = dep[i] + s * fw[i] - feq_p[opp[i]];
+    }
+}
+
+/* One step f_in -> f_out (Eq. 4.4 then streaming).  gfield: [D][N] acceleration
+ * or NULL.  With walls, bcm ([rho, u_1..u_D, theta][N]) holds the previous
+ * step's moments on entry (the wall targets) and this step's on return. */
+int or_step(const or_lattice* L, const or_params* P, const double* f_in, double* f_out, const double* gfield,
+            double* bcm) {
     const long N = (long)P->nx * P->ny * P->nz;
     const int D = L->D, Q = L->Q;
     double* rho = malloc(sizeof(double) * N);
@@ -241,18 +392,38 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
     double* F = malloc(sizeof(double) * 3 * N);
     double* Fsc = malloc(sizeof(double) * 3 * N);
     double* gT = malloc(sizeof(double) * 3 * N);
-    if (!rho || !th || !psi || !u || !F || !Fsc || !gT) {
-        free(rho); free(th); free(psi); free(u); free(F); free(Fsc); free(gT);
+    double* fc = P->walls ? malloc(sizeof(double) * (size_t)Q * N) : NULL;
+    if (!rho || !th || !psi || !u || !F || !Fsc || !gT || (P->walls && (!fc || !bcm))) {
+        free(rho); free(th); free(psi); free(u); free(F); free(Fsc); free(gT); free(fc);
         return -1;
     }
+    if (P->walls) {
+        or_wall_complete(L, P, f_in, fc, gfield, bcm);
+        f_in = fc;
+    }
     or_macros(L, P, f_in, gfield, rho, u, th, F, psi, Fsc);
+    if (P->walls) {
+        for (long n = 0; n < N; ++n) {
+            bcm[n] = rho[n];
+            for (int a = 0; a < D; ++a) bcm[(long)(1 + a) * N + n] = u[(long)a * N + n];
+            bcm[(long)(1 + D) * N + n] = th[n];
+        }
+    }
     if (P->use_H) {
         #pragma omp parallel for schedule(static)
         for (long n = 0; n < N; ++n) {
+            const long y = (n / P->nx) % P->ny;
             for (int a = 0; a < D; ++a) {
                 int cp[3] = {0, 0, 0}, cm[3] = {0, 0, 0};
                 cp[a] = 1; cm[a] = -1;
-                gT[(long)a * N + n] = 0.5 * (th[nbr(P, n, cp)] - th[nbr(P, n, cm)]);
+                if (P->walls && a == 1 && (y == 0 || y == P->ny - 1)) {
+                    /* wall rows: one-sided second-order difference into the fluid */
+                    const double sg = (y == 0) ? 1.0 : -1.0;
+                    const long n1 = n + (long)sg * P->nx, n2 = n + 2 * (long)sg * P->nx;
+                    gT[(long)a * N + n] = sg * (-3.0 * th[n] + 4.0 * th[n1] - th[n2]) / 2.0;
+                } else {
+                    gT[(long)a * N + n] = 0.5 * (th[nbr(P, n, cp)] - th[nbr(P, n, cm)]);
+                }
             }
         }
     }
@@ -279,15 +450,16 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
             f_out[(long)i * N + nbr(P, n, L->c[i])] = fstar;
         }
     }
-    free(rho); free(th); free(psi); free(u); free(F); free(Fsc); free(gT);
+    free(rho); free(th); free(psi); free(u); free(F); free(Fsc); free(gT); free(fc);
     return 0;
 }
 
 /* nsteps steps; f holds the state before and after, tmp is scratch of the same size. */
-int or_run(const or_lattice* L, const or_params* P, double* f, double* tmp, const double* gfield, int nsteps) {
+int or_run(const or_lattice* L, const or_params* P, double* f, double* tmp, const double* gfield, int nsteps,
+           double* bcm) {
     const long N = (long)P->nx * P->ny * P->nz;
     for (int t = 0; t < nsteps; ++t) {
-        if (or_step(L, P, f, tmp, gfield)) return -1;
+        if (or_step(L, P, f, tmp, gfield, bcm)) return -1;
         memcpy(f, tmp, sizeof(double) * (size_t)L->Q * N);
     }
     return 0;

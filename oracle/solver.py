@@ -45,7 +45,8 @@ class _Par(C.Structure):
                 ("g_uniform", C.c_double * 3), ("use_H", C.c_int), ("Pr", C.c_double),
                 ("use_SC", C.c_int), ("use_P", C.c_int), ("eos", C.c_int),
                 ("eos_a", C.c_double), ("eos_b", C.c_double), ("eos_T", C.c_double),
-                ("k", C.c_double)]
+                ("k", C.c_double), ("walls", C.c_int), ("wall_rule", C.c_int),
+                ("wall_u", (C.c_double * 3) * 2), ("wall_theta", C.c_double * 2)]
 
 
 _lib = None
@@ -56,8 +57,9 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(str(build()))
         dp = C.POINTER(C.c_double)
-        _lib.or_step.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp]
-        _lib.or_run.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, C.c_int]
+        _lib.or_step.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp]
+        _lib.or_run.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, C.c_int, dp]
+        _lib.or_wall_complete.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp]
         _lib.or_init.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp]
         _lib.or_macros.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp, dp, dp, dp, dp]
         _lib.or_feq.argtypes = [C.POINTER(_Lat), C.c_int, C.c_double, dp, C.c_double, dp]
@@ -109,6 +111,15 @@ def make_params_struct(L: _lat.Lattice, nx, ny, nz, tau_hat, p: dict) -> _Par:
     s.eos_b = float(p.get("eos_b", 0.0))
     s.eos_T = float(p.get("eos_T", 0.0))
     s.k = float(p.get("k", 0.0))
+    s.walls = 1 if p.get("walls", False) else 0
+    s.wall_rule = int(p.get("wall_rule", 0))
+    wu = p.get("wall_u", ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)))
+    wt = p.get("wall_theta", (1.0, 1.0))
+    for side in range(2):
+        v = list(wu[side]) + [0.0] * 3
+        for a in range(3):
+            s.wall_u[side][a] = float(v[a])
+        s.wall_theta[side] = float(wt[side])
     return s
 
 
@@ -137,6 +148,9 @@ class Oracle:
         self._tmp = np.zeros_like(self.f)
         self.g = None
         self.step_count = 0
+        # walls: the previous step's moments [rho, u_1..u_D, theta] (targets of Eqs. 4.7-4.8)
+        self.walls = bool(self.params.get("walls", False))
+        self.bcm = np.zeros((self.L.D + 2, self.N)) if self.walls else None
 
     @property
     def shape(self):
@@ -151,6 +165,8 @@ class Oracle:
     def init(self, rho, u, theta):
         r, uu, t = self._flat(rho), self._flat(u, self.L.D), self._flat(theta)
         lib().or_init(C.byref(self._ls), C.byref(self._ps), _ptr(r), _ptr(uu), _ptr(t), _ptr(self.f))
+        if self.walls:
+            self.bcm[0], self.bcm[1:1 + self.L.D], self.bcm[1 + self.L.D] = r, uu, t
         self.step_count = 0
 
     def set_force_field(self, g):
@@ -159,7 +175,7 @@ class Oracle:
 
     def run(self, nsteps: int):
         rc = lib().or_run(C.byref(self._ls), C.byref(self._ps), _ptr(self.f), _ptr(self._tmp),
-                          _ptr(self.g), int(nsteps))
+                          _ptr(self.g), int(nsteps), _ptr(self.bcm))
         if rc != 0:
             raise MemoryError("oracle step failed to allocate")
         self.step_count += nsteps
@@ -169,7 +185,13 @@ class Oracle:
         out = {k: np.zeros(N) for k in ("rho", "theta", "psi")}
         for k in ("u", "F", "Fsc"):
             out[k] = np.zeros((3, N))
-        lib().or_macros(C.byref(self._ls), C.byref(self._ps), _ptr(self.f), _ptr(self.g),
+        f = self.f
+        if self.walls:
+            # the state holds what streaming delivered; the wall completes it first
+            f = np.empty_like(self.f)
+            lib().or_wall_complete(C.byref(self._ls), C.byref(self._ps), _ptr(self.f), _ptr(f), _ptr(self.g),
+                                   _ptr(self.bcm))
+        lib().or_macros(C.byref(self._ls), C.byref(self._ps), _ptr(f), _ptr(self.g),
                         _ptr(out["rho"]), _ptr(out["u"]), _ptr(out["theta"]), _ptr(out["F"]),
                         _ptr(out["psi"]), _ptr(out["Fsc"]))
         res = {}
