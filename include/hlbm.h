@@ -15,7 +15,8 @@
  *   F^SC pseudopotential force (Eq. 3.8) over the lattice's reach-3 stencil
  *   P_i  pressure-tensor source (Eqs. 3.10-3.12)
  * All sources at time t use fields of time t at every node (no time lag).
- * Domains are periodic in every direction.
+ * Domains are periodic in every direction, or (D2Q37, HLBM_WALLS) periodic in
+ * x between two Tamm-Mott-Smith walls below and above (Sec. 4.3).
  *
  * Conventions
  *   Units: lattice units (dx = dt = 1), integer velocities c_i, lattice
@@ -68,9 +69,27 @@ typedef enum {
 #define HLBM_SRC_SC 4u         /* pseudopotential force F^SC (Eq. 3.8) */
 #define HLBM_SRC_P 8u          /* pressure-tensor source P_i (Eq. 3.12), needs SC */
 #define HLBM_ISOTHERMAL 16u    /* theta == 1 in f^eq and F_i (Sec. 5.4); required by SC */
+/* Walls (Sec. 4.3, Eqs. 4.7-4.8; the cases of Sec. 5.1-5.3), D2Q37 in the
+ * thermal mode without F^SC: rows 0 and ny - 1 are wall nodes and the
+ * solid-liquid interfaces lie half a cell inside them (y = 1/2, ny - 3/2), so
+ * the fluid layer is ny - 2 high; x stays periodic.  After streaming, the
+ * populations that come from beyond a wall are replaced, at a node r rows
+ * from its wall node, by
+ *     f_i = f*_ibar(x) + s f^eq_i(rho_p, u_i, theta_i) - f^eq_ibar(rho_p, u_p, theta_p)
+ * (Eq. 4.7): f*_ibar(x) is the population that left x in the opposite
+ * direction at the last streaming, (rho_p, u_p, theta_p) the node's moments
+ * of the previous step, (u_i, theta_i) the wall's velocity and temperature
+ * (params->wall_u, wall_theta) extrapolated linearly from the interface,
+ * through the first fluid row's previous moments, to the point where the
+ * population turned back (r - |c_iy| / 2 rows from the wall node), and s
+ * keeps the mass that left equal to the mass returned (impermeable wall).
+ * grad theta for H_i is one-sided into the fluid at the wall rows.  Each step
+ * is two launches (moments, then collision); the context keeps the previous
+ * step's moments (4 N floats, part of the state that hlbm_save writes). */
+#define HLBM_WALLS 32u
 
 typedef struct {
-  uint32_t flags;     /* HLBM_SRC_* | HLBM_ISOTHERMAL */
+  uint32_t flags;     /* HLBM_SRC_* | HLBM_ISOTHERMAL | HLBM_WALLS */
   double force[3];    /* uniform acceleration g when no force field is set */
   double Pr;          /* Prandtl number for H_i (Sec. 3.2), > 0 */
   int eos;            /* 0: van der Waals p = rho T/(1 - b rho) - a rho^2;
@@ -79,6 +98,8 @@ typedef struct {
   double k;           /* free parameter k of Eq. 3.12 */
   double rho0;        /* reference density of the stored deviations, > 0 */
   int storage;        /* hlbm_storage */
+  double wall_u[2][3];    /* HLBM_WALLS: velocity of the bottom (0) and top (1) wall, x only */
+  double wall_theta[2];   /* HLBM_WALLS: their temperature theta, > 0 */
 } hlbm_source_params;
 
 typedef struct hlbm_ctx hlbm_ctx;
@@ -142,7 +163,8 @@ hlbm_status hlbm_load(hlbm_ctx* ctx, const void* host_buf, size_t bytes);
 /* Steps taken since hlbm_init / hlbm_load. */
 long long hlbm_step_count(const hlbm_ctx* ctx);
 
-/* Schedule of the fused step: tile rows per CTA (2D: 4, 8 or 16; D3Q39: 4
+/* Schedule of the fused periodic step (wall-bounded contexts accept and
+ * ignore it: they have one schedule): tile rows per CTA (2D: 4, 8 or 16; D3Q39: 4
  * or 8; 0 = default 8), nodes per thread (1, or 2 on paired FP32 lanes
  * with 8 or 16 rows; 0 = default 2; D2Q37 only) and persistent CTAs that
  * prefetch their next tile (0 = default off, 1 = off, 2 = on, 3 = on and, on

@@ -15,7 +15,7 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / "libhlbm.so"
 
 HLBM_D2Q37, HLBM_D3Q39 = 0, 1
 HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2
-HLBM_SRC_FORCE, HLBM_SRC_H, HLBM_SRC_SC, HLBM_SRC_P, HLBM_ISOTHERMAL = 1, 2, 4, 8, 16
+HLBM_SRC_FORCE, HLBM_SRC_H, HLBM_SRC_SC, HLBM_SRC_P, HLBM_ISOTHERMAL, HLBM_WALLS = 1, 2, 4, 8, 16, 32
 STATUS = {0: "HLBM_OK", 1: "HLBM_EINVAL", 2: "HLBM_ENOMEM", 3: "HLBM_ECUDA", 4: "HLBM_EDIVERGED",
           5: "HLBM_ETIMEOUT", 6: "HLBM_ESTATE", 7: "HLBM_EUNSUPPORTED"}
 for _k, _v in STATUS.items():
@@ -33,7 +33,8 @@ EXPORTS = ["hlbm_workspace_bytes", "hlbm_create", "hlbm_bind_memory", "hlbm_set_
 class hlbm_source_params(C.Structure):
     _fields_ = [("flags", C.c_uint32), ("force", C.c_double * 3), ("Pr", C.c_double), ("eos", C.c_int),
                 ("eos_a", C.c_double), ("eos_b", C.c_double), ("eos_T", C.c_double), ("k", C.c_double),
-                ("rho0", C.c_double), ("storage", C.c_int)]
+                ("rho0", C.c_double), ("storage", C.c_int), ("wall_u", (C.c_double * 3) * 2),
+                ("wall_theta", C.c_double * 2)]
 
 
 class HLBMError(RuntimeError):

@@ -49,6 +49,11 @@ struct hlbm_ctx {
   int force_mode = FORCE_NONE;
   long long steps = 0;
 
+  // walls (HLBM_WALLS): [4][N] moments rho, u_x, u_y, theta - 1 of the
+  // previous step (mom[cur]) and of the step being taken (mom[cur ^ 1])
+  bool walls = false;
+  float* mom[2] = {nullptr, nullptr};
+
   bool failed = false;
   std::string msg;
 
@@ -84,7 +89,7 @@ static const int kGraphSteps = 32;  // even: a replay returns to the same buffer
 namespace {
 
 struct Layout {
-  size_t pop_bytes, off_pop1, off_g, off_part, off_red, off_flags, nflags, total;
+  size_t pop_bytes, off_pop1, off_g, off_part, off_red, off_flags, nflags, off_mom, mom_bytes, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -103,7 +108,10 @@ Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) 
   L.off_flags = L.off_red + 256;
   // D2Q37: one completion counter per tile row of the smallest tiles (4 rows)
   L.nflags = (lattice == 0) ? (size_t)((ny + 3) / 4) : 0;
-  L.total = L.off_flags + align256(L.nflags * 4);
+  L.off_mom = L.off_flags + align256(L.nflags * 4);
+  // walls: two [4][N] FP32 moment fields (previous step, this step)
+  L.mom_bytes = (p->flags & HLBM_WALLS) ? align256((size_t)4 * (size_t)N * 4) : 0;
+  L.total = L.off_mom + 2 * L.mom_bytes;
   return L;
 }
 
@@ -144,7 +152,7 @@ hlbm_status validate(int lattice, int nx, int ny, int nz, double tau_hat, const 
   if (!finite(tau_hat) || !(tau_hat > 0.5)) { why = "tau_hat must be finite and > 1/2"; return HLBM_EINVAL; }
   if (p->storage < HLBM_F32 || p->storage > HLBM_BF16) { why = "unknown storage"; return HLBM_EINVAL; }
   if (!finite(p->rho0) || !(p->rho0 > 0)) { why = "rho0 must be finite and > 0"; return HLBM_EINVAL; }
-  const uint32_t known = HLBM_SRC_FORCE | HLBM_SRC_H | HLBM_SRC_SC | HLBM_SRC_P | HLBM_ISOTHERMAL;
+  const uint32_t known = HLBM_SRC_FORCE | HLBM_SRC_H | HLBM_SRC_SC | HLBM_SRC_P | HLBM_ISOTHERMAL | HLBM_WALLS;
   if (p->flags & ~known) { why = "unknown flag bits"; return HLBM_EINVAL; }
   for (int d = 0; d < 3; ++d)
     if (!finite(p->force[d])) { why = "force must be finite"; return HLBM_EINVAL; }
@@ -167,6 +175,18 @@ hlbm_status validate(int lattice, int nx, int ny, int nz, double tau_hat, const 
   }
   if (lattice == HLBM_D3Q39 && (p->flags & (HLBM_SRC_H | HLBM_SRC_SC))) {
     why = "D3Q39 supports the body-force source only"; return HLBM_EUNSUPPORTED;
+  }
+  if (p->flags & HLBM_WALLS) {
+    if (lattice != HLBM_D2Q37) { why = "walls are built for D2Q37"; return HLBM_EUNSUPPORTED; }
+    if (p->flags & (HLBM_SRC_SC | HLBM_ISOTHERMAL)) {
+      why = "walls are built for the thermal mode without the pseudopotential force"; return HLBM_EUNSUPPORTED;
+    }
+    for (int k = 0; k < 2; ++k) {
+      if (!finite(p->wall_theta[k]) || !(p->wall_theta[k] > 0)) { why = "wall temperatures must be > 0"; return HLBM_EINVAL; }
+      for (int d = 0; d < 3; ++d)
+        if (!finite(p->wall_u[k][d])) { why = "wall velocities must be finite"; return HLBM_EINVAL; }
+      if (p->wall_u[k][1] != 0.0) { why = "walls move along x only (no normal velocity)"; return HLBM_EINVAL; }
+    }
   }
   return HLBM_OK;
 }
@@ -201,6 +221,8 @@ void carve(hlbm_ctx* c) {
   c->ms_ctr = reinterpret_cast<unsigned long long*>(c->arena + L.off_red + 224);
   c->flags = L.nflags ? reinterpret_cast<unsigned*>(c->arena + L.off_flags) : nullptr;
   c->nflags = L.nflags;
+  c->mom[0] = L.mom_bytes ? reinterpret_cast<float*>(c->arena + L.off_mom) : nullptr;
+  c->mom[1] = L.mom_bytes ? reinterpret_cast<float*>(c->arena + L.off_mom + L.mom_bytes) : nullptr;
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -356,7 +378,47 @@ hlbm_status check_status(hlbm_ctx* c) {
   return HLBM_OK;
 }
 
+WallArgs make_wall_args(const hlbm_ctx* c) {
+  WallArgs w{};
+  w.N = c->N;
+  w.nx = c->nx;
+  w.ny = c->ny;
+  w.gfield = c->gfield;
+  w.force_mode = c->force_mode;
+  for (int d = 0; d < 3; ++d) w.g[d] = (float)c->p.force[d];
+  w.rho0 = (float)c->p.rho0;
+  w.omega = (float)(1.0 / c->tau_hat);
+  w.beta = (float)(1.0 - 0.5 / c->tau_hat);
+  w.h_coef = (c->p.flags & HLBM_SRC_H) ? (float)(1.0 - 1.0 / c->p.Pr) : 0.f;
+  for (int k = 0; k < 2; ++k) {
+    w.wall_u[k][0] = (float)c->p.wall_u[k][0];
+    w.wall_u[k][1] = (float)c->p.wall_u[k][1];
+    w.wall_tb[k] = (float)(c->p.wall_theta[k] - 1.0);
+  }
+  // stored deviations are taken from the rest equilibrium at the mean wall temperature
+  const double tbr = 0.5 * (c->p.wall_theta[0] + c->p.wall_theta[1]) - 1.0;
+  w.tb_ref = (float)tbr;
+  w.e_ref = (float)(c->p.rho0 * 2.0 * D2Q37::cs2 * tbr);
+  w.mprev = c->mom[c->cur];
+  w.fin = c->pop[c->cur];
+  return w;
+}
+
+// One wall-bounded step: the moments launch (completed moments of time t into
+// mom[cur ^ 1]), then the collide launch.
+cudaError_t wall_step(hlbm_ctx* c) {
+  WallArgs w = make_wall_args(c);
+  w.mcur = c->mom[c->cur ^ 1];
+  cudaError_t e = launch_walls(w, c->storage, false, false, c->stream);
+  if (e != cudaSuccess) return e;
+  w.fout = c->pop[c->cur ^ 1];
+  e = launch_walls(w, c->storage, true, c->kind == KIND_THERMAL, c->stream);
+  c->cur ^= 1;
+  return e;
+}
+
 cudaError_t one_step(hlbm_ctx* c) {
+  if (c->walls) return wall_step(c);
   StepArgs a = make_args(c);
   a.fin = c->pop[c->cur];
   a.fout = c->pop[c->cur ^ 1];
@@ -370,7 +432,7 @@ cudaError_t one_step(hlbm_ctx* c) {
 // domain exactly, and a read region (pull 3 + neighbour frame H) within one
 // tile row of the tile.
 bool multistep_ok(const hlbm_ctx* c) {
-  if (!c->multistep || c->lattice != HLBM_D2Q37 || !c->flags) return false;
+  if (!c->multistep || c->lattice != HLBM_D2Q37 || !c->flags || c->walls) return false;
   const int H = c->kind == KIND_SC ? 3 : (c->kind == KIND_THERMAL ? 1 : 0);
   return c->nx % 32 == 0 && c->ny % c->rows == 0 && H + 3 <= c->rows;
 }
@@ -425,7 +487,7 @@ hlbm_status usable(hlbm_ctx* c) {
 namespace hlbm {
 // accessors used by the batched step (batch.cu)
 bool ctx_batchable(const hlbm_ctx* c, int* storage, int* kind, int* nx, int* ny) {
-  if (!c || c->lattice != HLBM_D2Q37 || !c->initialised || c->failed) return false;
+  if (!c || c->lattice != HLBM_D2Q37 || !c->initialised || c->failed || c->walls) return false;
   *storage = c->storage;
   *kind = c->kind;
   *nx = c->nx;
@@ -481,6 +543,7 @@ hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat, con
   c->elem = p->storage == HLBM_F32 ? 4 : 2;
   c->kind = (p->flags & HLBM_SRC_SC) ? KIND_SC : (p->flags & HLBM_SRC_H) ? KIND_THERMAL : KIND_LOCAL;
   c->force_mode = (p->flags & HLBM_SRC_FORCE) ? FORCE_UNIFORM : FORCE_NONE;
+  c->walls = (p->flags & HLBM_WALLS) != 0;
   c->rows = 8;
   // TMA needs a row pitch that is a multiple of 16 bytes
   const char* no_tma = std::getenv("HLBM_NO_TMA");
@@ -556,7 +619,12 @@ hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float
   cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess && c->flags) e = cudaMemsetAsync(c->flags, 0, c->nflags * 4, c->stream);
-  if (e == cudaSuccess) e = launch_init(c->lattice, a, c->storage, c->stream);
+  if (e == cudaSuccess && !c->walls) e = launch_init(c->lattice, a, c->storage, c->stream);
+  if (e == cudaSuccess && c->walls) {
+    WallArgs w = make_wall_args(c);
+    w.fout = c->pop[0];
+    e = launch_wall_init(w, c->storage, a.rho, a.u, a.theta, c->mom[0], c->stream);
+  }
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);  // host buffers are borrowed
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   c->cur = 0;
@@ -657,7 +725,16 @@ hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on
     a.u_out = stage + n;
     a.theta_out = stage + (1 + c->D) * n;
   }
-  cudaError_t e = launch_step(c, a, true);
+  cudaError_t e;
+  if (c->walls) {
+    WallArgs w = make_wall_args(c);
+    w.rho_out = a.rho_out;
+    w.u_out = a.u_out;
+    w.theta_out = a.theta_out;
+    e = launch_walls(w, c->storage, false, false, c->stream);
+  } else {
+    e = launch_step(c, a, true);
+  }
   if (e == cudaSuccess && !on_device) {
     if (rho) e = cudaMemcpyAsync(rho, stage, n * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, stage + n, c->D * n * 4, cudaMemcpyDeviceToHost, c->stream);
@@ -678,7 +755,13 @@ hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
   StepArgs a = make_args(c);
   a.fin = c->pop[c->cur];
   a.partials = c->partials;
-  HLBM_CUDA(c, launch_step(c, a, true), "moments kernel");
+  if (c->walls) {
+    WallArgs w = make_wall_args(c);
+    w.partials = c->partials;
+    HLBM_CUDA(c, launch_walls(w, c->storage, false, false, c->stream), "moments kernel");
+  } else {
+    HLBM_CUDA(c, launch_step(c, a, true), "moments kernel");
+  }
   const int nb = moment_blocks(c->lattice, c->nx, c->ny, c->nz);
   HLBM_CUDA(c, launch_reduce_partials(c->partials, nb, c->red, c->stream), "reduce kernel");
   double s[8];
@@ -699,7 +782,7 @@ hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
 
 size_t hlbm_state_bytes(const hlbm_ctx* c) {
   if (!c) return 0;
-  return 64 + (size_t)c->Q * (size_t)c->N * c->elem;
+  return 64 + (size_t)c->Q * (size_t)c->N * c->elem + (c->walls ? (size_t)16 * (size_t)c->N : 0);
 }
 
 hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
@@ -709,8 +792,12 @@ hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
   if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
   long long hdr[8] = {0x484c424d31LL, c->lattice, c->nx, c->ny, c->nz, c->storage, c->steps, 0};
   std::memcpy(host_buf, hdr, sizeof(hdr));
-  HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64, c->pop[c->cur], (size_t)c->Q * c->N * c->elem,
-                               cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  const size_t pbytes = (size_t)c->Q * c->N * c->elem;
+  HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64, c->pop[c->cur], pbytes, cudaMemcpyDeviceToHost,
+                               c->stream), "cudaMemcpyAsync");
+  if (c->walls)   // the wall targets: the previous step's moments
+    HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64 + pbytes, c->mom[c->cur], (size_t)16 * c->N,
+                                 cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   return HLBM_OK;
 }
@@ -729,8 +816,12 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
   if ((st = ensure_stream(c)) != HLBM_OK) return st;
   carve(c);
   if (c->lattice == 0) HLBM_CUDA(c, configure_step_d2q37(c->storage), "cudaFuncSetAttribute");
-  HLBM_CUDA(c, cudaMemcpyAsync(c->pop[0], static_cast<const char*>(host_buf) + 64, (size_t)c->Q * c->N * c->elem,
-                               cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  const size_t pbytes = (size_t)c->Q * c->N * c->elem;
+  HLBM_CUDA(c, cudaMemcpyAsync(c->pop[0], static_cast<const char*>(host_buf) + 64, pbytes, cudaMemcpyHostToDevice,
+                               c->stream), "cudaMemcpyAsync");
+  if (c->walls)
+    HLBM_CUDA(c, cudaMemcpyAsync(c->mom[0], static_cast<const char*>(host_buf) + 64 + pbytes, (size_t)16 * c->N,
+                                 cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
   if (c->flags) HLBM_CUDA(c, cudaMemsetAsync(c->flags, 0, c->nflags * 4, c->stream), "cudaMemsetAsync");
@@ -821,7 +912,8 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   if (steps < 1 || ckpt_every < 1 || !workspace || !dLdg || !loss) return fail(c, HLBM_EINVAL, "bad adjoint arguments");
   if (c->force_mode != FORCE_FIELD)
     return fail(c, HLBM_EINVAL, "the gradient is taken with respect to a force field: call hlbm_set_force_field(kind 1)");
-  if (c->p.flags & (HLBM_SRC_H | HLBM_SRC_SC)) return fail(c, HLBM_EUNSUPPORTED, "the adjoint covers the body-force step");
+  if (c->p.flags & (HLBM_SRC_H | HLBM_SRC_SC | HLBM_WALLS))
+    return fail(c, HLBM_EUNSUPPORTED, "the adjoint covers the periodic body-force step");
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return fail(c, HLBM_EINVAL, "workspace must be 256-byte aligned");
   const int K = std::min(ckpt_every, steps);
   const AdjLayout L = adj_layout(c, steps, K);

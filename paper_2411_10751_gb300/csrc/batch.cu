@@ -183,7 +183,7 @@ hlbm_status hlbm_batch_create(int n, hlbm_ctx* const* ctxs, hlbm_batch** out) {
   for (int k = 0; k < n; ++k) {
     int st, kind, nx, ny;
     if (!ctxs[k] || !ctx_batchable(ctxs[k], &st, &kind, &nx, &ny)) {
-      std::fprintf(stderr, "hlbm_batch_create: context %d is not an initialised D2Q37 context\n", k);
+      std::fprintf(stderr, "hlbm_batch_create: context %d is not an initialised periodic D2Q37 context\n", k);
       return HLBM_EINVAL;
     }
     if (storage >= 0 && st != storage) {

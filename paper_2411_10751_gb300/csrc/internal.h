@@ -59,6 +59,31 @@ struct StepArgs {
   unsigned long long* ms_ctr;
 };
 
+// Arguments of the wall-bounded D2Q37 step (walls.cu): moments and collide
+// launches of one step.
+struct WallArgs {
+  const void* fin;        // post-collision state of step t - 1, [Q][N]
+  void* fout;             // collide: state written by this step
+  const float* mprev;     // [4][N] rho, u_x, u_y, theta - 1 of the previous step (completed)
+  float* mcur;            // moments: this step's [4][N] (may be null); collide: read for grad theta
+  float* rho_out;         // moments readout (may be null)
+  float* u_out;
+  float* theta_out;
+  double* partials;       // moments: per-block FP64 sums [blocks][8] (may be null)
+  const float* gfield;
+  int force_mode;
+  float g[3];
+  long long N;
+  int nx, ny;
+  float rho0;
+  float omega, beta;
+  float h_coef;           // 1 - 1/Pr (H_i)
+  float wall_u[2][2];     // velocity of the bottom (0) and top (1) wall
+  float wall_tb[2];       // their temperature minus 1
+  float tb_ref;           // reference temperature of the stored deviations minus 1
+  float e_ref;            // rho0 D c0^2 tb_ref: energy moment of the reference offset
+};
+
 // Arguments of the initialisation kernel.
 struct InitArgs {
   const float* rho;
@@ -91,6 +116,15 @@ cudaError_t launch_init(int lattice, const InitArgs& a, int storage, cudaStream_
 cudaError_t launch_reduce_partials(const double* partials, int blocks, double* out, cudaStream_t s);
 // Number of CTAs a moments-mode launch with these sizes uses (size of the partials).
 int moment_blocks(int lattice, int nx, int ny, int nz);
+
+// Wall-bounded D2Q37 step (walls.cu): collide false = the moments launch
+// (completion, moments into mcur / the readout pointers, partials), true =
+// the collide launch (thermal: with H_i).
+cudaError_t launch_walls(const WallArgs& a, int storage, bool collide, bool thermal, cudaStream_t s);
+// Initial state of a wall-bounded context into a.fout and m [4][N] = rho,
+// u_x, u_y, theta - 1 of the initial fields.
+cudaError_t launch_wall_init(const WallArgs& a, int storage, const float* rho, const float* u, const float* theta,
+                             float* m, cudaStream_t s);
 
 // Adjoint of the body-force step (adjoint.cu).  seed: lambda_T, dL/dg and
 // per-block kinetic-energy sums (adjoint_seed_blocks(N) blocks, stride 8) from

@@ -32,6 +32,15 @@ def make_params(params: dict, storage: str = "f32") -> abi.hlbm_source_params:
         flags |= abi.HLBM_SRC_P
     if params.get("isothermal"):
         flags |= abi.HLBM_ISOTHERMAL
+    if params.get("walls"):
+        flags |= abi.HLBM_WALLS
+        wu = params.get("wall_u", ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)))
+        wt = params.get("wall_theta", (1.0, 1.0))
+        for side in range(2):
+            v = list(wu[side]) + [0.0, 0.0, 0.0]
+            for a in range(3):
+                p.wall_u[side][a] = float(v[a])
+            p.wall_theta[side] = float(wt[side])
     p.flags = flags
     g = list(params.get("g", (0.0, 0.0, 0.0))) + [0.0, 0.0, 0.0]
     for a in range(3):

@@ -284,7 +284,7 @@ def _wall_params(u_bottom=(0.0, 0.0), u_top=(0.0, 0.0), theta_bottom=1.0, theta_
 
 
 def couette(nx: int = 50, ny: int = 56, nu: float = 0.01, Re: float = 100.0, Pr: float = 0.71,
-            Ec: float = 10.0, theta_top: float = 0.8, steps: int = 1000) -> Case:
+            Ec: float = 10.0, theta_top: float = 0.8, steps: int = 1000, developed: bool = False) -> Case:
     """Thermal Couette flow (Sec. 5.1, Fig. 3): walls below row 0 and above row
     ny - 1 with the solid-liquid interfaces half a cell inside the wall rows,
     H = ny - 2 (50 x 56 gives the paper's 54); the top wall moves at
@@ -292,26 +292,33 @@ def couette(nx: int = 50, ny: int = 56, nu: float = 0.01, Re: float = 100.0, Pr:
     theta_top - Delta theta with Ec = u0^2 / (c_p Delta theta), c_p = 2 c0^2
     (Eq. 5.3, the specific heat at constant pressure of the D2Q37 gas in units
     of theta).  nu = c0^2 (tau^ - 1/2) as in Sec. 5.1.  The fluid starts at
-    rest at theta_top (Sec. 5.1) with rho = 1.  The thermal source H_i sets Pr."""
+    rest at theta_top (Sec. 5.1) with rho = 1, or (developed=True) in the
+    profiles of Eqs. 5.1-5.2 (y* from the bottom interface) with
+    rho theta = theta_top.  The thermal source H_i sets Pr."""
     H = ny - 2
     u0 = Re * nu / H
     dth = u0 * u0 / (2.0 * CS2_D2Q37 * Ec)
     tau = 0.5 + nu / CS2_D2Q37
     p = _wall_params(u_top=(u0, 0.0), theta_bottom=theta_top - dth, theta_top=theta_top,
                      H=(Pr != 1.0), Pr=Pr, rho0=1.0)
-    return Case("couette", "D2Q37", nx, ny, 1, tau, p, np.ones((ny, nx)), np.zeros((2, ny, nx)),
-                np.full((ny, nx), theta_top), None, steps,
+    rho, u, theta = np.ones((ny, nx)), np.zeros((2, ny, nx)), np.full((ny, nx), theta_top)
+    if developed:
+        ys = ((np.arange(ny, dtype=np.float64) - 0.5) / H)[:, None]
+        u[0] = np.broadcast_to(u0 * ys, (ny, nx))
+        theta = np.broadcast_to(theta_top - dth + dth * (ys + 0.5 * Pr * Ec * ys * (1.0 - ys)), (ny, nx)).copy()
+        rho = theta_top / theta
+    return Case("couette", "D2Q37", nx, ny, 1, tau, p, rho, u, theta, None, steps,
                 meta=dict(H=H, u0=u0, dtheta=dth, Ec=Ec, Pr=Pr, nu=nu, theta_bottom=theta_top - dth,
                           theta_top=theta_top))
 
 
 def poiseuille(nx: int = 50, ny: int = 56, nu: float = 0.01, Re: float = 100.0, Pr: float = 0.71,
-               Ec: float = 10.0, theta_top: float = 0.8, steps: int = 1000) -> Case:
+               Ec: float = 10.0, theta_top: float = 0.8, steps: int = 1000, developed: bool = False) -> Case:
     """Thermal Poiseuille flow (Sec. 5.2, Fig. 6): both walls at rest, the top at
     theta_top, the bottom Delta theta colder; a uniform acceleration g along x
     drives the flow.  Centre-line speed u_c = Re nu / H, g = 8 nu u_c / H^2
     (Eq. 5.4 with rho0 theta0 = 1), Ec = u_c^2 / (c_p Delta theta).  Geometry,
-    nu and the initial state as in couette()."""
+    nu and the initial state as in couette() (developed: Eqs. 5.4-5.5)."""
     H = ny - 2
     uc = Re * nu / H
     g = 8.0 * nu * uc / (H * H)
@@ -319,30 +326,47 @@ def poiseuille(nx: int = 50, ny: int = 56, nu: float = 0.01, Re: float = 100.0, 
     tau = 0.5 + nu / CS2_D2Q37
     p = _wall_params(theta_bottom=theta_top - dth, theta_top=theta_top, force=True, g=(g, 0.0, 0.0),
                      H=(Pr != 1.0), Pr=Pr, rho0=1.0)
-    return Case("poiseuille", "D2Q37", nx, ny, 1, tau, p, np.ones((ny, nx)), np.zeros((2, ny, nx)),
-                np.full((ny, nx), theta_top), None, steps,
+    rho, u, theta = np.ones((ny, nx)), np.zeros((2, ny, nx)), np.full((ny, nx), theta_top)
+    if developed:
+        ys = ((np.arange(ny, dtype=np.float64) - 0.5) / H)[:, None]
+        u[0] = np.broadcast_to(4.0 * uc * ys * (1.0 - ys), (ny, nx))
+        theta = np.broadcast_to(theta_top - dth + dth * (ys + Pr * Ec / 3.0 * (1.0 - (1.0 - 2.0 * ys) ** 4)),
+                                (ny, nx)).copy()
+        rho = theta_top / theta
+    return Case("poiseuille", "D2Q37", nx, ny, 1, tau, p, rho, u, theta, None, steps,
                 meta=dict(H=H, uc=uc, g=g, dtheta=dth, Ec=Ec, Pr=Pr, nu=nu))
 
 
 def rayleigh_benard(nx: int = 200, ny: int = 102, Ra: float = 10000.0, Pr: float = 1.41, nu: float = 0.04,
-                    theta_hot: float = 1.4, theta_cold: float = 1.0, steps: int = 1000) -> Case:
+                    theta_hot: float = 1.4, theta_cold: float = 1.0, steps: int = 1000,
+                    roll: float = 0.0) -> Case:
     """Rayleigh-Benard convection (Sec. 5.3, Fig. 9): L = nx, H = ny - 2 (200 x 102
     gives the paper's L = 200, H = 100), periodic in x, the bottom wall hot and
     the top wall cold, gravity -g along y with g from Eq. 5.6,
     Ra = 2 Pr g (theta_h - theta_c) H^3 / (nu^2 (theta_h + theta_c)).
+    Eq. 5.6 takes the expansion coefficient at the mean temperature
+    theta_m = (theta_h + theta_c) / 2, so nu is read at theta_m too: the
+    model's viscosity c0^2 theta (tau^ - 1/2) equals nu at theta_m.
     Initial temperature (Eq. 5.7, y measured up from the bottom interface, hot
     at the bottom): theta = theta_h - (theta_h - theta_c) y / H
     + 0.01 (theta_h - theta_c) sin(pi x / L) sin(pi y / H); rho = 1 / theta
-    (uniform pressure), u = 0.  Body force F_i and H_i are on (Sec. 5.3)."""
+    (uniform pressure), u = 0, or (roll > 0) the pair of convection rolls of
+    stream function roll (H / pi) sin(2 pi x / L) sin(pi y / H) (peak speed
+    about roll).  Body force F_i and H_i are on (Sec. 5.3)."""
     H = ny - 2
     dth = theta_hot - theta_cold
     g = Ra * nu * nu * (theta_hot + theta_cold) / (2.0 * Pr * dth * H ** 3)
-    tau = 0.5 + nu / CS2_D2Q37
+    tau = 0.5 + nu / (CS2_D2Q37 * 0.5 * (theta_hot + theta_cold))
     x = np.arange(nx, dtype=np.float64)[None, :]
     y = np.arange(ny, dtype=np.float64)[:, None] - 0.5          # distance from the bottom interface
     theta = theta_hot - dth * y / H + 0.01 * dth * np.sin(np.pi * x / nx) * np.sin(np.pi * y / H)
     theta = np.broadcast_to(theta, (ny, nx)).copy()
     p = _wall_params(theta_bottom=theta_hot, theta_top=theta_cold, force=True, g=(0.0, -g, 0.0),
                      H=(Pr != 1.0), Pr=Pr, rho0=1.0 / theta_cold)
-    return Case("rayleigh_benard", "D2Q37", nx, ny, 1, tau, p, 1.0 / theta, np.zeros((2, ny, nx)), theta,
+    u = np.zeros((2, ny, nx))
+    if roll:
+        kx, ky = 2.0 * np.pi / nx, np.pi / H
+        u[0] = np.broadcast_to(roll * (ky * H / np.pi) * np.sin(kx * x) * np.cos(ky * y), (ny, nx))
+        u[1] = np.broadcast_to(-roll * (kx * H / np.pi) * np.cos(kx * x) * np.sin(ky * y), (ny, nx))
+    return Case("rayleigh_benard", "D2Q37", nx, ny, 1, tau, p, 1.0 / theta, u, theta,
                 None, steps, meta=dict(H=H, L=nx, Ra=Ra, g=g, dtheta=dth, Pr=Pr, nu=nu))
