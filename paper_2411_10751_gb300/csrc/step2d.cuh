@@ -357,6 +357,10 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
     // the density's rounding error matters where F^SC amplifies it
     if constexpr (KIND == KIND_SC) K[0] = vadd(K[0], dr_l);
     apply_poly_h<L, 15>(g, K, om1, dr);
+    // 16-bit storage: stochastic rounding keyed by node and result (step_common.cuh)
+    uint32_t salt[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) salt[k] = std::is_same<T, float>::value ? 0u : node_salt(nodek[k], lane(g[0], k));
     if (TMA_STORE && a.tma_store) {
       // stage the tile's results densely in the (now unused) input planes and
       // write each plane with one bulk tensor store; out-of-domain rows and
@@ -365,7 +369,8 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
       static_for<37>([&](auto I) {
         constexpr int i = I;
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) sp[i * Cf::PLANE + (ty + k * TR) * BX + tx] = from_float<T>(lane(g[i], k));
+        for (int k = 0; k < NPT; ++k)
+          sp[i * Cf::PLANE + (ty + k * TR) * BX + tx] = round_store<T>(lane(g[i], k), pop_bits(salt[k], i));
       });
       fence_proxy_async_smem();
       __syncthreads();
@@ -384,7 +389,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
         T* __restrict__ fout = static_cast<T*>(fout_v) + nodek[k];
         static_for<37>([&](auto I) {
           constexpr int i = I;
-          Cf::C::st(fout + (size_t)i * (size_t)a.N, lane(g[i], k));
+          fout[(size_t)i * (size_t)a.N] = round_store<T>(lane(g[i], k), pop_bits(salt[k], i));
         });
       }
     }

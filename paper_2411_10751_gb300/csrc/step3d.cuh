@@ -7,6 +7,8 @@
 // a uniform, per-row or full acceleration field.
 #pragma once
 
+#include <type_traits>
+
 #include "step_common.cuh"
 #include "tma.cuh"
 
@@ -128,9 +130,11 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas3<MOM, NPT>()))
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
       if (!activek[k]) continue;
+      // 16-bit storage: stochastic rounding keyed by node and result (step_common.cuh)
+      const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(nodek[k], lane(g[0], k));
       static_for<L::Q>([&](auto I) {
         constexpr int i = I;
-        C::st(fout + (size_t)i * (size_t)a.N + nodek[k], lane(g[i], k));
+        fout[(size_t)i * (size_t)a.N + nodek[k]] = round_store<T>(lane(g[i], k), pop_bits(salt, i));
       });
     }
   }
@@ -319,9 +323,10 @@ __global__ void __launch_bounds__(128, 3)
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (!activek[k]) continue;
+      const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(nodek[k], lane(g[0], k));
       static_for<L::Q>([&](auto I) {
         constexpr int i = I;
-        C::st(fout + (size_t)i * (size_t)a.N + nodek[k], lane(g[i], k));
+        fout[(size_t)i * (size_t)a.N + nodek[k]] = round_store<T>(lane(g[i], k), pop_bits(salt, i));
       });
     }
     t = tn;

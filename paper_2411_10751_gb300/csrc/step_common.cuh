@@ -81,6 +81,44 @@ __device__ __forceinline__ void d3_cyz(int p, int& cy, int& cz, iseq<I...>) {
   ((cy = (p == I) ? D3Q39::c(I, 1) : cy), ...);
   ((cz = (p == I) ? D3Q39::c(I, 2) : cz), ...);
 }
+// --------------------------------------------------- rounding of step results
+// Results of a step are rounded to 16-bit storage stochastically: uniform
+// random bits are added below the kept mantissa (13 bits for FP16, 16 for
+// BF16) and the sum is truncated toward zero, so the stored value is the
+// FP32 value on average.  Round-to-nearest gives equal values equal errors:
+// a smooth field (neighbouring nodes, successive steps) then accumulates one
+// coherent error that the viscosity does not damp, which at 1024^2 left FP16
+// at twice its 256^2 error.  The random bits are a hash of the node index and
+// of the bits of the node's post-collision rest population (so they change
+// from step to step while the field changes, and a run is reproducible bit
+// for bit whatever the schedule); the mixing function is the 32-bit
+// finalizer of MurmurHash3 (Appleby).  Below the normal range (|v| < 2^-14
+// for FP16) the truncation drops more than 13 bits and rounds toward zero
+// more often; those values are a few FP16 subnormal steps from zero.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t node_salt(long long node, float g0) {
+  return fmix32((uint32_t)node * 0x9E3779B1u ^ __float_as_uint(g0));
+}
+// random bits for population i of a node with salt h (a second, cheap mix)
+__device__ __forceinline__ uint32_t pop_bits(uint32_t h, int i) {
+  return (h ^ ((uint32_t)i * 0x27D4EB2Fu)) * 0x165667B1u;
+}
+template <class T> __device__ __forceinline__ T round_store(float v, uint32_t bits);
+template <> __device__ __forceinline__ float round_store<float>(float v, uint32_t) { return v; }
+template <> __device__ __forceinline__ __half round_store<__half>(float v, uint32_t bits) {
+  return __float2half_rz(__uint_as_float(__float_as_uint(v) + (bits >> 19)));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 round_store<__nv_bfloat16>(float v, uint32_t bits) {
+  return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (bits >> 16)));
+}
+
 // exact for values that came from to_float of the same type
 template <class T> __device__ __forceinline__ T from_float(float v);
 template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
