@@ -26,6 +26,8 @@
  *        (theta-bar = theta - 1 enters f^eq and F_i only in thermal mode;
  *         the multiphase runs keep theta == 1, Sec. 5.4)
  *   2. grad theta by second-order central differences (Sec. 3.2).
+ *   (The single-pass variant, lag = 1, takes grad theta and F^SC / P_i from
+ *   the previous step's temperature and pseudopotential fields instead.)
  *   3. per node and velocity, the literal Table 2 polynomials:
  *        f^eq_i (Eq. 2.2 scaled), F_i (Eq. 3.3 scaled), H_i (Eq. 3.7
  *        scaled), P_i (Eq. 3.12 scaled); S_i = F_i + H_i + P_i.
@@ -80,6 +82,8 @@ typedef struct {
     int wall_rule;      /* 0: the reading of Eqs. 4.7-4.8 used; 1: Eq. 4.7 as printed */
     double wall_u[2][3];     /* velocity of the bottom (0) and top (1) wall */
     double wall_theta[2];    /* temperature of the bottom and top wall */
+    int lag;            /* 1: neighbour fields (theta for grad theta, psi for F^SC and P_i)
+                           of the previous step: the single-pass variant */
 } or_params;
 
 #define G_SC (-1.0)
@@ -181,8 +185,11 @@ void or_sources(const or_lattice* L, const or_params* P, double rho, const doubl
 }
 
 /* Step 1: macroscopic fields at every node (two passes: rho/psi, then the rest). */
-void or_macros(const or_lattice* L, const or_params* P, const double* f, const double* gfield,
-               double* rho, double* u, double* theta, double* F, double* psi, double* Fsc) {
+/* psi_field: the pseudopotential field F^SC and P_i use (NULL: psi of this
+ * step's densities; the previous step's in the lagged variant). */
+void or_macros_psi(const or_lattice* L, const or_params* P, const double* f, const double* gfield,
+                   const double* psi_field, double* rho, double* u, double* theta, double* F, double* psi,
+                   double* Fsc) {
     const long N = (long)P->nx * P->ny * P->nz;
     const int D = L->D, Q = L->Q;
     const double s = L->cs2;
@@ -191,7 +198,7 @@ void or_macros(const or_lattice* L, const or_params* P, const double* f, const d
         double r = 0.0;
         for (int i = 0; i < Q; ++i) r += f[(long)i * N + n];
         rho[n] = r;
-        psi[n] = P->use_SC ? or_psi(P, s, r) : 0.0;
+        psi[n] = P->use_SC ? (psi_field ? psi_field[n] : or_psi(P, s, r)) : 0.0;
     }
     #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
@@ -235,6 +242,11 @@ void or_macros(const or_lattice* L, const or_params* P, const double* f, const d
         }
         theta[n] = (e - rho[n] * uu + 0.5 * G2) / (rho[n] * D * s);
     }
+}
+
+void or_macros(const or_lattice* L, const or_params* P, const double* f, const double* gfield,
+               double* rho, double* u, double* theta, double* F, double* psi, double* Fsc) {
+    or_macros_psi(L, P, f, gfield, NULL, rho, u, theta, F, psi, Fsc);
 }
 
 /* Tamm-Mott-Smith wall boundary (Sec. 4.3, Eqs. 4.7-4.8): walls below row 0
@@ -380,9 +392,12 @@ void or_wall_complete(const or_lattice* L, const or_params* P, const double* f, 
 
 /* One step f_in -> f_out (Eq. 4.4 then streaming).  gfield: [D][N] acceleration
  * or NULL.  With walls, bcm ([rho, u_1..u_D, theta][N]) holds the previous
- * step's moments on entry (the wall targets) and this step's on return. */
+ * step's moments on entry (the wall targets) and this step's on return.
+ * With lag, lagf ([theta, psi][N]) holds the previous step's temperature and
+ * pseudopotential on entry (the neighbour fields of this step) and this
+ * step's on return. */
 int or_step(const or_lattice* L, const or_params* P, const double* f_in, double* f_out, const double* gfield,
-            double* bcm) {
+            double* bcm, double* lagf) {
     const long N = (long)P->nx * P->ny * P->nz;
     const int D = L->D, Q = L->Q;
     double* rho = malloc(sizeof(double) * N);
@@ -393,7 +408,7 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
     double* Fsc = malloc(sizeof(double) * 3 * N);
     double* gT = malloc(sizeof(double) * 3 * N);
     double* fc = P->walls ? malloc(sizeof(double) * (size_t)Q * N) : NULL;
-    if (!rho || !th || !psi || !u || !F || !Fsc || !gT || (P->walls && (!fc || !bcm))) {
+    if (!rho || !th || !psi || !u || !F || !Fsc || !gT || (P->walls && (!fc || !bcm)) || (P->lag && !lagf)) {
         free(rho); free(th); free(psi); free(u); free(F); free(Fsc); free(gT); free(fc);
         return -1;
     }
@@ -401,7 +416,7 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
         or_wall_complete(L, P, f_in, fc, gfield, bcm);
         f_in = fc;
     }
-    or_macros(L, P, f_in, gfield, rho, u, th, F, psi, Fsc);
+    or_macros_psi(L, P, f_in, gfield, P->lag ? lagf + N : NULL, rho, u, th, F, psi, Fsc);
     if (P->walls) {
         for (long n = 0; n < N; ++n) {
             bcm[n] = rho[n];
@@ -409,6 +424,9 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
             bcm[(long)(1 + D) * N + n] = th[n];
         }
     }
+    /* neighbour temperatures of grad theta: this step's, or the previous
+     * step's in the lagged variant */
+    const double* thn = P->lag ? lagf : th;
     if (P->use_H) {
         #pragma omp parallel for schedule(static)
         for (long n = 0; n < N; ++n) {
@@ -420,11 +438,19 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
                     /* wall rows: one-sided second-order difference into the fluid */
                     const double sg = (y == 0) ? 1.0 : -1.0;
                     const long n1 = n + (long)sg * P->nx, n2 = n + 2 * (long)sg * P->nx;
-                    gT[(long)a * N + n] = sg * (-3.0 * th[n] + 4.0 * th[n1] - th[n2]) / 2.0;
+                    gT[(long)a * N + n] = sg * (-3.0 * thn[n] + 4.0 * thn[n1] - thn[n2]) / 2.0;
                 } else {
-                    gT[(long)a * N + n] = 0.5 * (th[nbr(P, n, cp)] - th[nbr(P, n, cm)]);
+                    gT[(long)a * N + n] = 0.5 * (thn[nbr(P, n, cp)] - thn[nbr(P, n, cm)]);
                 }
             }
+        }
+    }
+    if (P->lag) {
+        /* this step's temperature and pseudopotential: the next step's neighbour fields */
+        #pragma omp parallel for schedule(static)
+        for (long n = 0; n < N; ++n) {
+            lagf[n] = th[n];
+            lagf[N + n] = P->use_SC ? or_psi(P, L->cs2, rho[n]) : 0.0;
         }
     }
     const double tau = P->tau_hat;
@@ -456,10 +482,10 @@ int or_step(const or_lattice* L, const or_params* P, const double* f_in, double*
 
 /* nsteps steps; f holds the state before and after, tmp is scratch of the same size. */
 int or_run(const or_lattice* L, const or_params* P, double* f, double* tmp, const double* gfield, int nsteps,
-           double* bcm) {
+           double* bcm, double* lagf) {
     const long N = (long)P->nx * P->ny * P->nz;
     for (int t = 0; t < nsteps; ++t) {
-        if (or_step(L, P, f, tmp, gfield, bcm)) return -1;
+        if (or_step(L, P, f, tmp, gfield, bcm, lagf)) return -1;
         memcpy(f, tmp, sizeof(double) * (size_t)L->Q * N);
     }
     return 0;

@@ -46,7 +46,7 @@ class _Par(C.Structure):
                 ("use_SC", C.c_int), ("use_P", C.c_int), ("eos", C.c_int),
                 ("eos_a", C.c_double), ("eos_b", C.c_double), ("eos_T", C.c_double),
                 ("k", C.c_double), ("walls", C.c_int), ("wall_rule", C.c_int),
-                ("wall_u", (C.c_double * 3) * 2), ("wall_theta", C.c_double * 2)]
+                ("wall_u", (C.c_double * 3) * 2), ("wall_theta", C.c_double * 2), ("lag", C.c_int)]
 
 
 _lib = None
@@ -57,8 +57,9 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(str(build()))
         dp = C.POINTER(C.c_double)
-        _lib.or_step.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp]
-        _lib.or_run.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, C.c_int, dp]
+        _lib.or_step.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp, dp]
+        _lib.or_run.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, C.c_int, dp, dp]
+        _lib.or_macros_psi.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp, dp, dp, dp, dp, dp]
         _lib.or_wall_complete.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp]
         _lib.or_init.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp]
         _lib.or_macros.argtypes = [C.POINTER(_Lat), C.POINTER(_Par), dp, dp, dp, dp, dp, dp, dp, dp]
@@ -120,6 +121,7 @@ def make_params_struct(L: _lat.Lattice, nx, ny, nz, tau_hat, p: dict) -> _Par:
         for a in range(3):
             s.wall_u[side][a] = float(v[a])
         s.wall_theta[side] = float(wt[side])
+    s.lag = 1 if p.get("lag", False) else 0
     return s
 
 
@@ -151,6 +153,9 @@ class Oracle:
         # walls: the previous step's moments [rho, u_1..u_D, theta] (targets of Eqs. 4.7-4.8)
         self.walls = bool(self.params.get("walls", False))
         self.bcm = np.zeros((self.L.D + 2, self.N)) if self.walls else None
+        # single-pass variant: the previous step's theta and psi [2, N]
+        self.lag = bool(self.params.get("lag", False))
+        self.lagf = np.zeros((2, self.N)) if self.lag else None
 
     @property
     def shape(self):
@@ -167,6 +172,14 @@ class Oracle:
         lib().or_init(C.byref(self._ls), C.byref(self._ps), _ptr(r), _ptr(uu), _ptr(t), _ptr(self.f))
         if self.walls:
             self.bcm[0], self.bcm[1:1 + self.L.D], self.bcm[1 + self.L.D] = r, uu, t
+        if self.lag:
+            self.lagf[0] = t
+            self.lagf[1] = 0.0
+            if self.params.get("SC"):
+                from . import eos
+                p = self.params
+                pe = eos.pressure(p.get("eos", "vdw"), r, p["eos_a"], p["eos_b"], p["eos_T"])
+                self.lagf[1] = np.sqrt(np.maximum(2.0 * (pe - r * self.L.cs2) / (-1.0 * self.L.cs2), 0.0))
         self.step_count = 0
 
     def set_force_field(self, g):
@@ -175,7 +188,7 @@ class Oracle:
 
     def run(self, nsteps: int):
         rc = lib().or_run(C.byref(self._ls), C.byref(self._ps), _ptr(self.f), _ptr(self._tmp),
-                          _ptr(self.g), int(nsteps), _ptr(self.bcm))
+                          _ptr(self.g), int(nsteps), _ptr(self.bcm), _ptr(self.lagf))
         if rc != 0:
             raise MemoryError("oracle step failed to allocate")
         self.step_count += nsteps
@@ -191,7 +204,8 @@ class Oracle:
             f = np.empty_like(self.f)
             lib().or_wall_complete(C.byref(self._ls), C.byref(self._ps), _ptr(self.f), _ptr(f), _ptr(self.g),
                                    _ptr(self.bcm))
-        lib().or_macros(C.byref(self._ls), C.byref(self._ps), _ptr(f), _ptr(self.g),
+        lib().or_macros_psi(C.byref(self._ls), C.byref(self._ps), _ptr(f), _ptr(self.g),
+                            _ptr(self.lagf[1].copy()) if self.lag else None,
                         _ptr(out["rho"]), _ptr(out["u"]), _ptr(out["theta"]), _ptr(out["F"]),
                         _ptr(out["psi"]), _ptr(out["Fsc"]))
         res = {}
