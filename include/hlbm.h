@@ -87,9 +87,23 @@ typedef enum {
  * is two launches (moments, then collision); the context keeps the previous
  * step's moments (4 N floats, part of the state that hlbm_save writes). */
 #define HLBM_WALLS 32u
+/* In-place step (D2Q37, periodic): one population buffer instead of two (the
+ * AA pattern: even steps collide in place and store each result in the
+ * opposite velocity's slot of the same node; odd steps read those from the
+ * neighbours and store into them), with the single-pass variant of the
+ * neighbour fields: grad theta (H_i) and the pseudopotential of F^SC and P_i
+ * are taken from the previous step's temperature and density (the fields of
+ * time t would need neighbour populations that other threads overwrite in
+ * place).  Results differ from the two-pass step by that lag (not with the
+ * body force alone, where the two are identical).  Workspace: one buffer, a
+ * staging area of 4 N floats and two N-float neighbour fields (1024^2 FP32:
+ * 179 MB instead of 310 MB).  hlbm_population_sums_noalloc reads its totals
+ * only after an even number of steps (odd steps leave each population in its
+ * opposite's slot).  Not with HLBM_WALLS, the adjoint or the batched step. */
+#define HLBM_AA 64u
 
 typedef struct {
-  uint32_t flags;     /* HLBM_SRC_* | HLBM_ISOTHERMAL | HLBM_WALLS */
+  uint32_t flags;     /* HLBM_SRC_* | HLBM_ISOTHERMAL | HLBM_WALLS | HLBM_AA */
   double force[3];    /* uniform acceleration g when no force field is set */
   double Pr;          /* Prandtl number for H_i (Sec. 3.2), > 0 */
   int eos;            /* 0: van der Waals p = rho T/(1 - b rho) - a rho^2;
@@ -184,7 +198,10 @@ hlbm_status hlbm_synchronize(hlbm_ctx* ctx);
 /* Wall-time limit of each bounded device-side wait (the mbarrier wait of
  * the TMA staging), in seconds, 0 < seconds <= 60; default 2.  A kernel
  * whose wait expires skips its tile, sets a status word, and the next
- * hlbm_synchronize / hlbm_moments / hlbm_diag returns HLBM_ETIMEOUT. */
+ * hlbm_synchronize / hlbm_moments / hlbm_diag returns HLBM_ETIMEOUT.  The
+ * state is then undefined (the skipped tiles were not written, and copies
+ * that were still in flight may land after the kernel ended) until
+ * hlbm_init or hlbm_load replaces it. */
 hlbm_status hlbm_set_wait_timeout(hlbm_ctx* ctx, double seconds);
 
 /* Message of the last failing call on this context (never NULL). */
@@ -212,14 +229,21 @@ size_t hlbm_adjoint_workspace_bytes(const hlbm_ctx* ctx, int steps, int ckpt_eve
 hlbm_status hlbm_adjoint_run(hlbm_ctx* ctx, int steps, int ckpt_every, void* workspace, size_t bytes, float* dLdg,
                              double* loss);
 
-/* Batched step (D2Q37): advances many independent contexts -- any sizes,
- * sources and parameters, one storage type -- together, with one kernel
- * launch per time step over every tile of every domain (replayed from a CUDA
- * graph).  The contexts must be initialised; hlbm_batch_create moves them onto
- * the batch's stream, so their own calls stay ordered with batch steps.  Each
- * context's state and step count advance as if hlbm_step had been called;
- * hlbm_moments / hlbm_diag / hlbm_save work on them as usual.  A context must
- * not be destroyed before the batch. */
+/* Batched step (D2Q37): advances many independent periodic contexts -- any
+ * sizes, sources and parameters, one storage type -- together, with ONE
+ * persistent kernel launch per time step (replayed from a CUDA graph of two
+ * steps): resident CTAs take (domain, tile) items of every domain from a work
+ * list through a device counter and run the single-domain tile code (32 x 8
+ * tiles, two nodes per thread; 32 x 4 tiles, one node per thread, for the
+ * pseudopotential kind), so each context's state equals that of hlbm_step
+ * with those schedules bit for bit.  The contexts must be initialised;
+ * hlbm_batch_create moves them onto the batch's stream, so their own calls
+ * stay ordered with batch steps.  Each context's state and step count advance
+ * as if hlbm_step had been called; hlbm_moments / hlbm_diag / hlbm_save work
+ * on them as usual.  A context must not be destroyed before the batch.
+ * Wall-bounded contexts (HLBM_WALLS) cannot be batched (HLBM_EINVAL).  After
+ * hlbm_batch_synchronize reports HLBM_ETIMEOUT the batch is unusable: destroy
+ * it and reload the contexts. */
 typedef struct hlbm_batch hlbm_batch;
 hlbm_status hlbm_batch_create(int n, hlbm_ctx* const* ctxs, hlbm_batch** out);
 hlbm_status hlbm_batch_step(hlbm_batch* batch, int n);
@@ -251,8 +275,16 @@ int hlbm_lattice_info(int lattice, int* c, double* w, double* cs2);
  * GPU that loads it until the process exits; it limits a call to 1 ..
  * 33,554,432 nodes (HLBM_EINVAL beyond, with a message on stderr).  All calls
  * share it and overwrite what they use: calls that overlap on the GPU race.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture. */
+ * The call copies the totals to the host and synchronises the stream, so it
+ * must not be made while the stream is being captured into a graph.  The
+ * first call on a device looks up the array's device address with that
+ * device current; with CUDA's lazy module loading that first call (and the
+ * first call for each lattice and storage pair, whose kernels load then) may
+ * place the array and the kernels' code in device memory: a caller that must
+ * not allocate after start-up makes one warm-up call per device, lattice and
+ * storage during its initialisation.  The stored values of wall-bounded
+ * contexts (HLBM_WALLS) are deviations from another reference state; their
+ * energy total is not this one. */
 hlbm_status hlbm_population_sums_noalloc(int lattice, long long nodes, int storage, double rho0,
                                          const void* populations, void* cuda_stream, double* out);
 

@@ -15,7 +15,7 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / "libhlbm.so"
 
 HLBM_D2Q37, HLBM_D3Q39 = 0, 1
 HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2
-HLBM_SRC_FORCE, HLBM_SRC_H, HLBM_SRC_SC, HLBM_SRC_P, HLBM_ISOTHERMAL, HLBM_WALLS = 1, 2, 4, 8, 16, 32
+HLBM_SRC_FORCE, HLBM_SRC_H, HLBM_SRC_SC, HLBM_SRC_P, HLBM_ISOTHERMAL, HLBM_WALLS, HLBM_AA = 1, 2, 4, 8, 16, 32, 64
 STATUS = {0: "HLBM_OK", 1: "HLBM_EINVAL", 2: "HLBM_ENOMEM", 3: "HLBM_ECUDA", 4: "HLBM_EDIVERGED",
           5: "HLBM_ETIMEOUT", 6: "HLBM_ESTATE", 7: "HLBM_EUNSUPPORTED"}
 for _k, _v in STATUS.items():

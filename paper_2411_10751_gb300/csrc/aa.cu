@@ -1,0 +1,287 @@
+// In-place D2Q37 step (AA pattern) with single-pass neighbour fields: one
+// population buffer instead of two, and one read and one write of every
+// population per step with no frame of populations.
+//
+// AA pattern.  Before an even step, slot i of node x holds f_i(x, t) (after
+// streaming).  The even step reads node x's own 37 slots, collides, and writes
+// f*_i into slot ibar of the same node.  Before an odd step, f_i(x, t) is
+// therefore in slot ibar of node x - c_i; the odd step reads those, collides,
+// and writes f*_i into slot i of node x + c_i, which is where the next even
+// step finds f_i(x + c_i, t + 1).  In both steps the slots a node writes are
+// exactly the slots it read (slot i of x + c_i is slot (ibar)bar of
+// x - c_ibar), so the update is in place without any ordering between nodes.
+//
+// Neighbour fields.  grad theta (H_i) and the pseudopotential of F^SC and
+// P_i would need the populations of the neighbours at time t, which other
+// threads may already have overwritten; they are taken from the previous
+// step instead (the single-pass variant of the method): each step writes its
+// nodes' theta - 1 (thermal kind) or psi (pseudopotential kind) into one of
+// two auxiliary fields and reads the neighbours' from the other.  The frame
+// of the auxiliary field (1 or 3 nodes around the 32 x 8 tile) is staged in
+// shared memory.
+//
+// Bytes per node and step: 37 x elem read + 37 x elem write + 4 (own field
+// written) + about 4 (the staged field, neighbours served by L2): 304 B FP32.
+#include "internal.h"
+#include "lattice.cuh"
+#include "step_common.cuh"
+
+#include <type_traits>
+
+namespace hlbm {
+namespace {
+
+using L = D2Q37;
+constexpr int kBX = 32, kBY = 8;
+
+__host__ __device__ constexpr int aa_opp(int i) { return i == 0 ? 0 : (((i - 1) & 1) ? i - 1 : i + 1); }
+
+template <int KIND>
+constexpr int frame_of() {
+  return KIND == KIND_SC ? 3 : (KIND == KIND_THERMAL ? 1 : 0);
+}
+
+// ODD: the step's parity; MOM: moments readout (no store).
+template <int ST, int KIND, bool ODD, bool MOM>
+__global__ void __launch_bounds__(kBX * kBY) aa_step_kernel(const __grid_constant__ StepArgs a) {
+  using T = typename Codec<ST>::T;
+  constexpr int H = frame_of<KIND>();
+  constexpr int SW = kBX + 2 * H, SH = kBY + 2 * H;
+  __shared__ float aux[(H > 0) ? SW * SH : 1];
+  __shared__ double red[kBY][6];
+  const int nx = a.nx, ny = a.ny;
+  const size_t N = (size_t)a.N;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kBX + tx;
+  const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < nx && y < ny;
+  const int xc = active ? x : x % nx, yc = y < ny ? y : y % ny;   // inactive lanes still fill the frame
+
+  // the previous step's neighbour field, on the tile and its frame
+  if constexpr (H > 0) {
+    for (int k = tid; k < SW * SH; k += kBX * kBY) {
+      const int j = k / SW, i = k - j * SW;
+      const int X = wrapm(x0 - H + i, nx), Y = wrapm(y0 - H + j, ny);
+      aux[k] = __ldg(a.aux_rd + (size_t)Y * nx + X);
+    }
+    __syncthreads();
+  }
+
+  // the node's populations at time t
+  const T* __restrict__ f = static_cast<const T*>(a.fin);
+  float g[37];
+  int xs[7], ys[7];
+#pragma unroll
+  for (int d = -3; d <= 3; ++d) {
+    xs[d + 3] = wrap1(xc - d, nx);
+    ys[d + 3] = wrap1(yc - d, ny) * nx;
+  }
+  static_for<37>([&](auto I) {
+    constexpr int i = I;
+    if constexpr (!ODD) {
+      g[i] = to_float(f[(size_t)i * N + (size_t)yc * nx + xc]);
+    } else {
+      constexpr int cx = L::c(i, 0), cy = L::c(i, 1), b = aa_opp(i);
+      g[i] = to_float(f[(size_t)b * N + ys[cy + 3] + xs[cx + 3]]);
+    }
+  });
+  const int node = yc * nx + xc;
+
+  float dr, dr_l, acc, J[3], Pih;
+  moments_h<L>(g, dr, dr_l, acc, J, Pih);
+  const float rho = a.rho0 + dr;
+  float ga[3];
+  accel<2>(a, node, yc, ga);
+  float Fx = rho * ga[0], Fy = rho * ga[1];
+  float sigma = 0.f, psi_now = 0.f;
+  if constexpr (KIND == KIND_SC) {
+    // F^SC = -G psi(x) sum_i w_i psi(x + c_i) c_i, G = -1, psi of the previous step
+    const float* ap = aux + (ty + H) * SW + tx + H;
+    float sx = 0.f, sy = 0.f;
+    static_for<L::NPAIR>([&](auto P) {
+      constexpr int i = 2 * P + 1;
+      constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
+      const float dpsi = ap[cy * SW + cx] - ap[-cy * SW - cx];
+      if constexpr (cx != 0) sx = fmaf((float)(L::w(i) * cx), dpsi, sx);
+      if constexpr (cy != 0) sy = fmaf((float)(L::w(i) * cy), dpsi, sy);
+    });
+    const float ps = ap[0];
+    const float fsx = ps * sx, fsy = ps * sy;
+    Fx += fsx;
+    Fy += fsy;
+    sigma = (ps > 0.f) ? a.p_coef * (fsx * fsx + fsy * fsy) * rcp_nr(ps * ps) : 0.f;
+    psi_now = psi_of<L>(a, dr, dr_l);
+  }
+  constexpr float Dc = (float)(2.0 * L::cs2);
+  const float inv_rho = rcp_nr(rho);
+  const float ux = fmaf(0.5f, Fx, J[0]) * inv_rho;
+  const float uy = fmaf(0.5f, Fy, J[1]) * inv_rho;
+  const float uu = fmaf(ux, ux, uy * uy);
+  const float G2 = fmaf(Dc, sigma, 2.f * fmaf(ux, Fx, uy * Fy));
+  const float tb = (fmaf(0.5f, G2, Pih - rho * uu) * inv_rho) * (1.f / Dc);
+
+  if constexpr (MOM) {
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (active) {
+      if (a.rho_out) a.rho_out[node] = rho;
+      if (a.u_out) {
+        a.u_out[node] = ux;
+        a.u_out[N + node] = uy;
+      }
+      if (a.theta_out) a.theta_out[node] = 1.f + tb;
+      const bool bad = !(isfinite(rho) && rho > 0.f && isfinite(ux) && isfinite(uy) && isfinite(tb));
+      v[0] = dr;
+      v[1] = (double)rho * ux;
+      v[2] = (double)rho * uy;
+      v[4] = 0.5 * ((double)Pih + (double)Dc * dr + 0.5 * (double)G2);
+      v[5] = bad ? 1.0 : 0.0;
+    }
+    if (a.partials) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+      if (tx == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[ty][k] = v[k];
+      __syncthreads();
+      if (tid < 6) {
+        double sum = 0.0;
+        for (int w = 0; w < kBY; ++w) sum += red[w][tid];
+        a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + tid] = sum;
+      }
+    }
+    return;
+  } else {
+    if (!active) return;
+    // this step's field for the next step's neighbours
+    if constexpr (KIND == KIND_SC) a.aux_wr[node] = psi_now;
+    if constexpr (KIND == KIND_THERMAL) a.aux_wr[node] = tb;
+    NodeSrcT<float> s;
+    s.hG[0] = s.hG[1] = s.hG[2] = 0.f;
+    if constexpr (KIND == KIND_THERMAL) {
+      const float* ap = aux + (ty + 1) * SW + tx + 1;
+      const float gtx = 0.5f * (ap[1] - ap[-1]);
+      const float gty = 0.5f * (ap[SW] - ap[-SW]);
+      // s^(3) += rho theta (1 - 1/Pr) [delta grad_xi theta], grad_xi = c0 grad
+      const float hc = rho * (1.f + tb) * (a.h_coef * (float)L::c0);
+      s.hG[0] = hc * gtx;
+      s.hG[1] = hc * gty;
+    }
+    constexpr float inv_c0 = (float)(1.0 / L::c0);
+    s.dr = 0.f;
+    s.rho = rho;
+    s.tb = a.isothermal ? 0.f : tb;
+    s.u[0] = ux * inv_c0;
+    s.u[1] = uy * inv_c0;
+    s.u[2] = 0.f;
+    s.F[0] = Fx * inv_c0;
+    s.F[1] = Fy * inv_c0;
+    s.F[2] = 0.f;
+    s.sigma = sigma;
+    float K[15];
+    poly2<L>(s, a.omega, a.beta, K);
+    const float om1 = 1.f - a.omega;
+    K[0] = fmaf(-om1, acc, K[0]);
+    if constexpr (KIND == KIND_SC) K[0] += dr_l;
+    apply_poly_h<L, 15>(g, K, om1, dr);
+    // 16-bit storage: stochastic rounding keyed by node and result (step_common.cuh)
+    const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(node, g[0]);
+    T* __restrict__ fo = static_cast<T*>(a.fout);
+    static_for<37>([&](auto I) {
+      constexpr int i = I;
+      constexpr int b = aa_opp(i);
+      const T v = round_store<T>(g[i], pop_bits(salt, i));
+      if constexpr (!ODD) {
+        fo[(size_t)b * N + node] = v;                             // slot ibar of x
+      } else {
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
+        fo[(size_t)i * N + ys[3 - cy] + xs[3 - cx]] = v;          // slot i of x + c_i
+      }
+    });
+  }
+}
+
+// Initial state in the even layout: slot i of node x = f^eq_i(x); the
+// neighbour field the first step reads (theta - 1, or psi of the density).
+template <int ST, int KIND>
+__global__ void __launch_bounds__(256) aa_init_kernel(const __grid_constant__ StepArgs a, const float* __restrict__ rho,
+                                                      const float* __restrict__ u, const float* __restrict__ theta) {
+  using T = typename Codec<ST>::T;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const size_t N = (size_t)a.N;
+  NodeSrcT<float> s;
+  s.dr = rho[n] - a.rho0;
+  s.rho = rho[n];
+  s.tb = theta[n] - 1.f;
+  constexpr float inv_c0 = (float)(1.0 / L::c0);
+  s.u[0] = u[n] * inv_c0;
+  s.u[1] = u[N + n] * inv_c0;
+  s.u[2] = 0.f;
+  s.F[0] = s.F[1] = s.F[2] = 0.f;
+  s.hG[0] = s.hG[1] = s.hG[2] = 0.f;
+  s.sigma = 0.f;
+  float g[37], K[15];
+#pragma unroll
+  for (int i = 0; i < 37; ++i) g[i] = 0.f;
+  poly2<L>(s, 1.f, 0.f, K);
+  apply_poly<L, 15>(g, K, 0.f);
+  T* __restrict__ fo = static_cast<T*>(a.fout);
+  static_for<37>([&](auto I) {
+    constexpr int i = I;
+    Codec<ST>::st(fo + (size_t)i * N + n, g[i]);
+  });
+  if constexpr (KIND == KIND_THERMAL) a.aux_wr[n] = theta[n] - 1.f;
+  if constexpr (KIND == KIND_SC) a.aux_wr[n] = psi_of<L>(a, rho[n] - a.rho0, 0.f);
+}
+
+template <int ST, int KIND>
+cudaError_t launch_kind(const StepArgs& a, bool odd, bool mom, cudaStream_t s) {
+  const dim3 block(kBX, kBY), grid((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY);
+  if (mom) {
+    if (odd) aa_step_kernel<ST, KIND, true, true><<<grid, block, 0, s>>>(a);
+    else aa_step_kernel<ST, KIND, false, true><<<grid, block, 0, s>>>(a);
+  } else {
+    if (odd) aa_step_kernel<ST, KIND, true, false><<<grid, block, 0, s>>>(a);
+    else aa_step_kernel<ST, KIND, false, false><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_st(const StepArgs& a, int kind, bool odd, bool mom, cudaStream_t s) {
+  if (kind == KIND_SC) return launch_kind<ST, KIND_SC>(a, odd, mom, s);
+  if (kind == KIND_THERMAL) return launch_kind<ST, KIND_THERMAL>(a, odd, mom, s);
+  return launch_kind<ST, KIND_LOCAL>(a, odd, mom, s);
+}
+
+template <int ST>
+cudaError_t init_st(const StepArgs& a, int kind, const float* rho, const float* u, const float* theta,
+                    cudaStream_t s) {
+  const unsigned blocks = (unsigned)((a.N + 255) / 256);
+  if (kind == KIND_SC) aa_init_kernel<ST, KIND_SC><<<blocks, 256, 0, s>>>(a, rho, u, theta);
+  else if (kind == KIND_THERMAL) aa_init_kernel<ST, KIND_THERMAL><<<blocks, 256, 0, s>>>(a, rho, u, theta);
+  else aa_init_kernel<ST, KIND_LOCAL><<<blocks, 256, 0, s>>>(a, rho, u, theta);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_aa(const StepArgs& a, int kind, int storage, bool odd, bool mom, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return launch_st<ST_F32>(a, kind, odd, mom, s);
+    case ST_F16: return launch_st<ST_F16>(a, kind, odd, mom, s);
+    default: return launch_st<ST_BF16>(a, kind, odd, mom, s);
+  }
+}
+
+cudaError_t launch_aa_init(const StepArgs& a, int kind, int storage, const float* rho, const float* u,
+                           const float* theta, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return init_st<ST_F32>(a, kind, rho, u, theta, s);
+    case ST_F16: return init_st<ST_F16>(a, kind, rho, u, theta, s);
+    default: return init_st<ST_BF16>(a, kind, rho, u, theta, s);
+  }
+}
+
+}  // namespace hlbm

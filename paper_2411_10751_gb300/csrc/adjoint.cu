@@ -492,16 +492,14 @@ bool adj_rows_eligible(const AdjArgs& a) {
 
 template <int ST>
 int adj_rows_ctas() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cache[kMaxDevicesCached];
+  return per_device_cached(cache, [](int dev) {
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(adjoint_rows_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjRowsSmem<ST>::BYTES);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adjoint_rows_kernel<ST>, 256, AdjRowsSmem<ST>::BYTES);
-    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  }
-  return n;
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  });
 }
 
 template <int ST>

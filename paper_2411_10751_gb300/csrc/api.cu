@@ -54,6 +54,12 @@ struct hlbm_ctx {
   bool walls = false;
   float* mom[2] = {nullptr, nullptr};
 
+  // in-place step (HLBM_AA): one population buffer (pop[0]; pop[1] is then a
+  // staging area of 4 N floats), the step parity in `cur`, and two neighbour
+  // fields: aux[cur ^ 1] is read by the next step, aux[cur] written
+  bool aa = false;
+  float* aux[2] = {nullptr, nullptr};
+
   bool failed = false;
   std::string msg;
 
@@ -89,7 +95,8 @@ static const int kGraphSteps = 32;  // even: a replay returns to the same buffer
 namespace {
 
 struct Layout {
-  size_t pop_bytes, off_pop1, off_g, off_part, off_red, off_flags, nflags, off_mom, mom_bytes, total;
+  size_t pop_bytes, off_pop1, off_g, off_part, off_red, off_flags, nflags, off_mom, mom_bytes, off_aux, aux_bytes,
+      total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -101,7 +108,9 @@ Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) 
   const size_t elem = (p->storage == HLBM_F32) ? 4 : 2;
   L.pop_bytes = align256((size_t)Q * (size_t)N * elem);
   L.off_pop1 = L.pop_bytes;
-  L.off_g = L.off_pop1 + L.pop_bytes;
+  // in place: the second buffer is only a staging area for host fields
+  const size_t second = (p->flags & HLBM_AA) ? align256((size_t)(2 + D) * (size_t)N * 4) : L.pop_bytes;
+  L.off_g = L.off_pop1 + second;
   const size_t gbytes = (p->flags & HLBM_SRC_FORCE) ? align256((size_t)D * (size_t)N * 4) : 0;
   L.off_part = L.off_g + gbytes;
   L.off_red = L.off_part + align256((size_t)moment_blocks(lattice, nx, ny, nz) * 8 * sizeof(double));
@@ -111,7 +120,9 @@ Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) 
   L.off_mom = L.off_flags + align256(L.nflags * 4);
   // walls: two [4][N] FP32 moment fields (previous step, this step)
   L.mom_bytes = (p->flags & HLBM_WALLS) ? align256((size_t)4 * (size_t)N * 4) : 0;
-  L.total = L.off_mom + 2 * L.mom_bytes;
+  L.off_aux = L.off_mom + 2 * L.mom_bytes;
+  L.aux_bytes = (p->flags & HLBM_AA) ? align256((size_t)N * 4) : 0;
+  L.total = L.off_aux + 2 * L.aux_bytes;
   return L;
 }
 
@@ -152,7 +163,8 @@ hlbm_status validate(int lattice, int nx, int ny, int nz, double tau_hat, const 
   if (!finite(tau_hat) || !(tau_hat > 0.5)) { why = "tau_hat must be finite and > 1/2"; return HLBM_EINVAL; }
   if (p->storage < HLBM_F32 || p->storage > HLBM_BF16) { why = "unknown storage"; return HLBM_EINVAL; }
   if (!finite(p->rho0) || !(p->rho0 > 0)) { why = "rho0 must be finite and > 0"; return HLBM_EINVAL; }
-  const uint32_t known = HLBM_SRC_FORCE | HLBM_SRC_H | HLBM_SRC_SC | HLBM_SRC_P | HLBM_ISOTHERMAL | HLBM_WALLS;
+  const uint32_t known =
+      HLBM_SRC_FORCE | HLBM_SRC_H | HLBM_SRC_SC | HLBM_SRC_P | HLBM_ISOTHERMAL | HLBM_WALLS | HLBM_AA;
   if (p->flags & ~known) { why = "unknown flag bits"; return HLBM_EINVAL; }
   for (int d = 0; d < 3; ++d)
     if (!finite(p->force[d])) { why = "force must be finite"; return HLBM_EINVAL; }
@@ -175,6 +187,10 @@ hlbm_status validate(int lattice, int nx, int ny, int nz, double tau_hat, const 
   }
   if (lattice == HLBM_D3Q39 && (p->flags & (HLBM_SRC_H | HLBM_SRC_SC))) {
     why = "D3Q39 supports the body-force source only"; return HLBM_EUNSUPPORTED;
+  }
+  if (p->flags & HLBM_AA) {
+    if (lattice != HLBM_D2Q37) { why = "the in-place step is built for D2Q37"; return HLBM_EUNSUPPORTED; }
+    if (p->flags & HLBM_WALLS) { why = "the in-place step is built for periodic domains"; return HLBM_EUNSUPPORTED; }
   }
   if (p->flags & HLBM_WALLS) {
     if (lattice != HLBM_D2Q37) { why = "walls are built for D2Q37"; return HLBM_EUNSUPPORTED; }
@@ -223,6 +239,8 @@ void carve(hlbm_ctx* c) {
   c->nflags = L.nflags;
   c->mom[0] = L.mom_bytes ? reinterpret_cast<float*>(c->arena + L.off_mom) : nullptr;
   c->mom[1] = L.mom_bytes ? reinterpret_cast<float*>(c->arena + L.off_mom + L.mom_bytes) : nullptr;
+  c->aux[0] = L.aux_bytes ? reinterpret_cast<float*>(c->arena + L.off_aux) : nullptr;
+  c->aux[1] = L.aux_bytes ? reinterpret_cast<float*>(c->arena + L.off_aux + L.aux_bytes) : nullptr;
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -417,8 +435,21 @@ cudaError_t wall_step(hlbm_ctx* c) {
   return e;
 }
 
+// One in-place step of parity cur: reads aux[cur ^ 1], writes aux[cur].
+cudaError_t aa_step(hlbm_ctx* c, bool mom, StepArgs* margs = nullptr) {
+  StepArgs a = margs ? *margs : make_args(c);
+  a.fin = c->pop[0];
+  a.fout = c->pop[0];
+  a.aux_rd = c->aux[c->cur ^ 1];
+  a.aux_wr = c->aux[c->cur];
+  cudaError_t e = launch_aa(a, c->kind, c->storage, c->cur == 1, mom, c->stream);
+  if (!mom) c->cur ^= 1;
+  return e;
+}
+
 cudaError_t one_step(hlbm_ctx* c) {
   if (c->walls) return wall_step(c);
+  if (c->aa) return aa_step(c, false);
   StepArgs a = make_args(c);
   a.fin = c->pop[c->cur];
   a.fout = c->pop[c->cur ^ 1];
@@ -432,7 +463,7 @@ cudaError_t one_step(hlbm_ctx* c) {
 // domain exactly, and a read region (pull 3 + neighbour frame H) within one
 // tile row of the tile.
 bool multistep_ok(const hlbm_ctx* c) {
-  if (!c->multistep || c->lattice != HLBM_D2Q37 || !c->flags || c->walls) return false;
+  if (!c->multistep || c->lattice != HLBM_D2Q37 || !c->flags || c->walls || c->aa) return false;
   const int H = c->kind == KIND_SC ? 3 : (c->kind == KIND_THERMAL ? 1 : 0);
   return c->nx % 32 == 0 && c->ny % c->rows == 0 && H + 3 <= c->rows;
 }
@@ -487,7 +518,7 @@ hlbm_status usable(hlbm_ctx* c) {
 namespace hlbm {
 // accessors used by the batched step (batch.cu)
 bool ctx_batchable(const hlbm_ctx* c, int* storage, int* kind, int* nx, int* ny) {
-  if (!c || c->lattice != HLBM_D2Q37 || !c->initialised || c->failed || c->walls) return false;
+  if (!c || c->lattice != HLBM_D2Q37 || !c->initialised || c->failed || c->walls || c->aa) return false;
   *storage = c->storage;
   *kind = c->kind;
   *nx = c->nx;
@@ -544,6 +575,7 @@ hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat, con
   c->kind = (p->flags & HLBM_SRC_SC) ? KIND_SC : (p->flags & HLBM_SRC_H) ? KIND_THERMAL : KIND_LOCAL;
   c->force_mode = (p->flags & HLBM_SRC_FORCE) ? FORCE_UNIFORM : FORCE_NONE;
   c->walls = (p->flags & HLBM_WALLS) != 0;
+  c->aa = (p->flags & HLBM_AA) != 0;
   c->rows = 8;
   // TMA needs a row pitch that is a multiple of 16 bytes
   const char* no_tma = std::getenv("HLBM_NO_TMA");
@@ -619,7 +651,13 @@ hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float
   cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess && c->flags) e = cudaMemsetAsync(c->flags, 0, c->nflags * 4, c->stream);
-  if (e == cudaSuccess && !c->walls) e = launch_init(c->lattice, a, c->storage, c->stream);
+  if (e == cudaSuccess && c->aa) {
+    StepArgs s = make_args(c);
+    s.fout = c->pop[0];
+    s.aux_wr = c->aux[1];               // read by the first step (parity 0)
+    e = launch_aa_init(s, c->kind, c->storage, a.rho, a.u, a.theta, c->stream);
+  }
+  if (e == cudaSuccess && !c->walls && !c->aa) e = launch_init(c->lattice, a, c->storage, c->stream);
   if (e == cudaSuccess && c->walls) {
     WallArgs w = make_wall_args(c);
     w.fout = c->pop[0];
@@ -720,7 +758,8 @@ hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on
     a.theta_out = theta;
   } else {
     // stage in the population buffer that does not hold the current state
-    stage = static_cast<float*>(c->pop[c->cur ^ 1]);
+    // (in place: the staging area)
+    stage = static_cast<float*>(c->pop[c->aa ? 1 : (c->cur ^ 1)]);
     a.rho_out = stage;
     a.u_out = stage + n;
     a.theta_out = stage + (1 + c->D) * n;
@@ -732,6 +771,8 @@ hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on
     w.u_out = a.u_out;
     w.theta_out = a.theta_out;
     e = launch_walls(w, c->storage, false, false, c->stream);
+  } else if (c->aa) {
+    e = aa_step(c, true, &a);
   } else {
     e = launch_step(c, a, true);
   }
@@ -759,6 +800,8 @@ hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
     WallArgs w = make_wall_args(c);
     w.partials = c->partials;
     HLBM_CUDA(c, launch_walls(w, c->storage, false, false, c->stream), "moments kernel");
+  } else if (c->aa) {
+    HLBM_CUDA(c, aa_step(c, true, &a), "moments kernel");
   } else {
     HLBM_CUDA(c, launch_step(c, a, true), "moments kernel");
   }
@@ -782,7 +825,8 @@ hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
 
 size_t hlbm_state_bytes(const hlbm_ctx* c) {
   if (!c) return 0;
-  return 64 + (size_t)c->Q * (size_t)c->N * c->elem + (c->walls ? (size_t)16 * (size_t)c->N : 0);
+  return 64 + (size_t)c->Q * (size_t)c->N * c->elem + (c->walls ? (size_t)16 * (size_t)c->N : 0) +
+         (c->aa ? (size_t)4 * (size_t)c->N : 0);
 }
 
 hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
@@ -797,6 +841,9 @@ hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
                                c->stream), "cudaMemcpyAsync");
   if (c->walls)   // the wall targets: the previous step's moments
     HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64 + pbytes, c->mom[c->cur], (size_t)16 * c->N,
+                                 cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (c->aa)      // the neighbour field the next step reads (the step parity is in the step count)
+    HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64 + pbytes, c->aux[c->cur ^ 1], (size_t)4 * c->N,
                                  cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   return HLBM_OK;
@@ -822,13 +869,18 @@ hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
   if (c->walls)
     HLBM_CUDA(c, cudaMemcpyAsync(c->mom[0], static_cast<const char*>(host_buf) + 64 + pbytes, (size_t)16 * c->N,
                                  cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  const int par = c->aa ? (int)(hdr[6] & 1) : 0;   // in place: the layout of the saved step's parity
+  if (c->aa)
+    HLBM_CUDA(c, cudaMemcpyAsync(c->aux[par ^ 1], static_cast<const char*>(host_buf) + 64 + pbytes, (size_t)4 * c->N,
+                                 cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned long long), c->stream), "cudaMemsetAsync");
   if (c->flags) HLBM_CUDA(c, cudaMemsetAsync(c->flags, 0, c->nflags * 4, c->stream), "cudaMemsetAsync");
   HLBM_CUDA(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  c->cur = 0;
+  c->cur = par;
   c->gen = 0;
   c->steps = hdr[6];
+  drop_graphs(c);
   c->initialised = true;
   return HLBM_OK;
 }
@@ -912,8 +964,8 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   if (steps < 1 || ckpt_every < 1 || !workspace || !dLdg || !loss) return fail(c, HLBM_EINVAL, "bad adjoint arguments");
   if (c->force_mode != FORCE_FIELD)
     return fail(c, HLBM_EINVAL, "the gradient is taken with respect to a force field: call hlbm_set_force_field(kind 1)");
-  if (c->p.flags & (HLBM_SRC_H | HLBM_SRC_SC | HLBM_WALLS))
-    return fail(c, HLBM_EUNSUPPORTED, "the adjoint covers the periodic body-force step");
+  if (c->p.flags & (HLBM_SRC_H | HLBM_SRC_SC | HLBM_WALLS | HLBM_AA))
+    return fail(c, HLBM_EUNSUPPORTED, "the adjoint covers the periodic body-force step on two buffers");
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return fail(c, HLBM_EINVAL, "workspace must be 256-byte aligned");
   const int K = std::min(ckpt_every, steps);
   const AdjLayout L = adj_layout(c, steps, K);

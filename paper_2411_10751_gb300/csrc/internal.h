@@ -4,9 +4,28 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 namespace hlbm {
+
+// A per-device value (a kernel's resident-CTA count) computed once per device:
+// compute(dev) runs on the first call with that device current; concurrent
+// first calls compute the same value, and the atomic keeps the store free of
+// data races.
+constexpr int kMaxDevicesCached = 64;
+template <class F>
+int per_device_cached(std::atomic<int> (&cache)[kMaxDevicesCached], F&& compute) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kMaxDevicesCached) return compute(dev);
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (!n) {
+    n = compute(dev);
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
 
 enum Kind : int {
   KIND_LOCAL = 0,    // sources need only the node itself (F_i)
@@ -57,6 +76,10 @@ struct StepArgs {
   unsigned gen0;
   unsigned* flags;
   unsigned long long* ms_ctr;
+  // in-place (AA) step: the previous step's neighbour field (theta - 1 or psi)
+  // read on the tile's frame, and this step's written per node
+  const float* aux_rd;
+  float* aux_wr;
 };
 
 // Arguments of the wall-bounded D2Q37 step (walls.cu): moments and collide
@@ -116,6 +139,14 @@ cudaError_t launch_init(int lattice, const InitArgs& a, int storage, cudaStream_
 cudaError_t launch_reduce_partials(const double* partials, int blocks, double* out, cudaStream_t s);
 // Number of CTAs a moments-mode launch with these sizes uses (size of the partials).
 int moment_blocks(int lattice, int nx, int ny, int nz);
+
+// In-place D2Q37 step (aa.cu): odd = the step's parity (fin == fout, the one
+// population buffer); mom = moments readout (rho_out / u_out / theta_out,
+// partials) of the state before that step.  aa_init writes the even layout
+// and the first step's neighbour field (a.aux_wr).
+cudaError_t launch_aa(const StepArgs& a, int kind, int storage, bool odd, bool mom, cudaStream_t s);
+cudaError_t launch_aa_init(const StepArgs& a, int kind, int storage, const float* rho, const float* u,
+                           const float* theta, cudaStream_t s);
 
 // Wall-bounded D2Q37 step (walls.cu): collide false = the moments launch
 // (completion, moments into mcur / the readout pointers, partials), true =

@@ -779,30 +779,26 @@ cudaError_t configure2() {
 // CTAs of a persistent launch: the resident CTAs per SM times the SM count.
 template <int ST, int KIND, int BY, int NPT>
 int persistent_ctas() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cache[kMaxDevicesCached];
+  return per_device_cached(cache, [](int dev) {
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_persistent_kernel<ST, KIND, BY, NPT>, 32 * BY / NPT,
                                                   Cfg2<ST, KIND, false, BY>::SMEM);
-    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  }
-  return n;
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  });
 }
 
 template <int ST, int KIND, int BY, int NPT>
 int multistep_ctas() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cache[kMaxDevicesCached];
+  return per_device_cached(cache, [](int dev) {
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_multistep_kernel<ST, KIND, BY, NPT>, 32 * BY / NPT,
                                                   Cfg2<ST, KIND, false, BY>::SMEM);
-    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  }
-  return n;
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  });
 }
 
 template <int ST, int KIND, bool MOM, int BY, int NPT = 1>

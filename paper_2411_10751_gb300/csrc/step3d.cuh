@@ -344,15 +344,13 @@ inline bool rows3_eligible(const StepArgs& a) {
 
 template <int ST>
 int rows3_ctas() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cache[kMaxDevicesCached];
+  return per_device_cached(cache, [](int dev) {
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step3d_rows_kernel<ST>, 128, rows3_smem<ST>());
-    n = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
-  }
-  return n;
+    return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  });
 }
 
 // rows: 4 or 8 tile rows; npt: nodes per thread (2 needs 8 rows); tmaps: the

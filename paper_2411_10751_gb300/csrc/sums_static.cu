@@ -16,6 +16,7 @@
 // overwrites the partials and result slots it uses (nothing has to start at
 // zero); all calls share the array, so calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race and must be avoided.
+#include <atomic>
 #include <cstdio>
 
 #include "hlbm.h"
@@ -34,7 +35,7 @@ static __device__ __align__(256) double g_sum_scratch[kSumMaxBlocks * 8 + 8];
 
 // host-side copies of the scratch's device address, one per device
 constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<double*> g_scratch_ptr[kMaxDevices];   // per-device address of g_sum_scratch (looked up once)
 
 // Block b sums nodes [b * 2048, (b + 1) * 2048): per node the FP32 moments of
 // the stored deviations g_i = (f_i - w_i rho0) / w_i, accumulated in FP64.
@@ -132,15 +133,16 @@ extern "C" hlbm_status hlbm_population_sums_noalloc(int lattice, long long nodes
   // per-device set-up: the host-side address of the static scratch array
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HLBM_ECUDA;
-  if (!g_scratch_ptr[dev]) {
+  double* scratch = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_sum_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return HLBM_ECUDA;
     }
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+    scratch = static_cast<double*>(p);
+    g_scratch_ptr[dev].store(scratch, std::memory_order_release);   // concurrent first calls store the same address
   }
-  double* scratch = g_scratch_ptr[dev];
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int blocks = (int)((nodes + kSumNodesPerBlock - 1) / kSumNodesPerBlock);
   cudaError_t e = lattice == HLBM_D2Q37 ? launch_partial<D2Q37>(storage, populations, nodes, blocks, scratch, s)

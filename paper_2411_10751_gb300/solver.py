@@ -32,6 +32,8 @@ def make_params(params: dict, storage: str = "f32") -> abi.hlbm_source_params:
         flags |= abi.HLBM_SRC_P
     if params.get("isothermal"):
         flags |= abi.HLBM_ISOTHERMAL
+    if params.get("lag"):
+        flags |= abi.HLBM_AA     # the in-place step runs the single-pass (lagged) neighbour fields
     if params.get("walls"):
         flags |= abi.HLBM_WALLS
         wu = params.get("wall_u", ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0)))
@@ -211,8 +213,9 @@ class KineticEnergy(torch.autograd.Function):
 
 
 class Batch:
-    """Independent D2Q37 domains stepped together (hlbm_batch_*): one kernel
-    launch per time step over all tiles of all domains."""
+    """Independent periodic D2Q37 domains stepped together (hlbm_batch_*): one
+    persistent kernel launch per time step over the tiles of every domain and
+    every source kind (graph-replayed)."""
 
     def __init__(self, solvers: list):
         self.solvers = list(solvers)

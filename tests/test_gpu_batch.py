@@ -5,7 +5,7 @@
 2. A batch step equals stepping every context on its own, bit for bit (both
    run the same tile code).
 3. The full workload: 256 domains of sides 32..256 (about 6.4 M nodes), 100
-   steps in graph-replayed batch launches; sampled domains against the oracle.
+   steps of the persistent batch launch; every domain against the oracle.
 """
 import numpy as np
 import pytest
@@ -73,9 +73,13 @@ def test_batch_domains_match_oracle(lib):
 
 
 def test_batch_equals_individual_steps_bitwise(lib):
+    """The batch runs the single-domain tile code (32 x 8 tiles, one node per
+    thread); that schedule on single contexts gives the same bits."""
     cases = _mixed_cases()
     batched = [_ctx(lib, c) for c in cases]
     single = [_ctx(lib, c) for c in cases]
+    for g in single:
+        g.set_tile(8, 1, 1)
     b = lib.Batch(batched)
     b.step(7)               # three graph replays of two steps and one single launch
     b.synchronize()
@@ -87,17 +91,44 @@ def test_batch_equals_individual_steps_bitwise(lib):
     b.close()
 
 
+def _oracle_worker_init():
+    import os
+    os.environ["OMP_NUM_THREADS"] = "1"     # one domain per process
+
+
+def _oracle_moments(args):
+    c, steps = args
+    return _oracle(c, steps)
+
+
 def test_full_batched_workload(lib):
+    """256 domains of sides 32..256 (about 6.4 M nodes), 100 steps in the
+    persistent batch launch, every domain against the FP64 oracle at 1e-5
+    (the oracle runs in a pool of spawned processes, one domain each)."""
+    import multiprocessing as mp
+    import os
     cases = W.batched(256, seed=0)
     ctxs = [_ctx(lib, c) for c in cases]
     b = lib.Batch(ctxs)
     b.step(100)
     b.synchronize()
-    sizes = np.array([c.nodes for c in cases])
-    sample = sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 0, 1, 101, 202, 255})
-    for k in sample:
-        e = _err(ctxs[k].moments_host(), _oracle(cases[k], 100))
-        assert max(e) < TOL32, (k, cases[k].name, cases[k].nx, e)
+    got = [g.moments_host() for g in ctxs]
     for g in ctxs:
         assert np.isfinite(g.diag()).all()
     b.close()
+    order = sorted(range(len(cases)), key=lambda k: -cases[k].nodes)   # largest first
+    with mp.get_context("spawn").Pool(max(1, (os.cpu_count() or 2)), initializer=_oracle_worker_init) as pool:
+        ref = dict(zip(order, pool.map(_oracle_moments, [(cases[k], 100) for k in order], chunksize=1)))
+    worst = np.zeros(3)
+    for k, c in enumerate(cases):
+        e = np.array(_err(got[k], ref[k]))
+        # A droplet's velocity is its spurious current (0.0035..0.009 on the
+        # small domains), and its liquid (rho 6.3) is stored as deviations of
+        # about 5.2 from the gas reference density: an FP32 ulp of 4.8e-7 per
+        # population, about 1e-7 in u after 100 steps.  u is compared on the
+        # velocity scale max(max|u|, 0.01) (the Kolmogorov domains' scale).
+        umax = np.sqrt((ref[k][1] ** 2).sum(0)).max()
+        e[1] *= umax / max(umax, 0.01)
+        worst = np.maximum(worst, e)
+        assert max(e) < TOL32, (k, c.name, c.nx, e)
+    print(f"256 domains, worst relative error rho {worst[0]:.2e} u {worst[1]:.2e} theta {worst[2]:.2e}")
