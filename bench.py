@@ -55,11 +55,28 @@ WORKLOADS = {
     "tg3d256": (lambda: W.taylor_green_3d(n=256), "D3Q39 compressible Taylor-Green 256^3, Ma=0.3, tau=0.6, body force"),
     "droplet512": (lambda: W.droplet(n=512), "D2Q37 vdW droplet 512x512 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8"),
     "droplet1024": (lambda: W.droplet(n=1024), "D2Q37 vdW droplet 1024x1024 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8"),
+    # the in-place (AA) step with single-pass neighbour fields
+    "thermal1024_aa": (lambda: _lagged(W.thermal_decay(n=1024)), WORKLOAD + ", in place (AA), single-pass"),
+    "droplet1024_aa": (lambda: _lagged(W.droplet(n=1024)),
+                       "D2Q37 vdW droplet 1024x1024 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8, in place (AA), single-pass"),
+    "kolmogorov4096_aa": (lambda: _lagged(W.kolmogorov(4096)),
+                          "D2Q37 Kolmogorov flow, 4096x4096 periodic, tau=0.8, g=1e-5, in place (AA)"),
 }
 
 
+def _lagged(case):
+    case.params = dict(case.params)
+    case.params["lag"] = True
+    return case
+
+
 def _bytes_per_node(case, storage):
-    return 2 * (37 if case.lattice == "D2Q37" else 39) * (4 if storage == "f32" else 2)
+    """Algorithmic bytes per lattice update: one read and one write of every
+    population (+ the in-place step's neighbour field, written and read once)."""
+    b = 2 * (37 if case.lattice == "D2Q37" else 39) * (4 if storage == "f32" else 2)
+    if case.params.get("lag") and (case.params.get("H") or case.params.get("SC")):
+        b += 8
+    return b
 
 
 def _set_force(g, case):
@@ -720,7 +737,8 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _ncu_traffic(khash, args.storage, sched),
                          "algorithmic_bytes_per_node": bytes_per_node,
-                         "kernel": (("step3d_rows_kernel" if sched[2] >= 2 and case.nx in (32, 64, 128, 256)
+                         "kernel": "aa_step_kernel (in place, one launch per step)" if case.params.get("lag") else
+                                   (("step3d_rows_kernel" if sched[2] >= 2 and case.nx in (32, 64, 128, 256)
                                      else "step3d_kernel") if case.lattice == "D3Q39" else
                                     ("step2d_multistep_kernel" if _multistep(case, sched) else
                                      "step2d_persistent_kernel" if sched[2] >= 2 else "step2d_kernel")) +

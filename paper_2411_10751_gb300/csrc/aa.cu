@@ -43,7 +43,7 @@ constexpr int frame_of() {
 
 // ODD: the step's parity; MOM: moments readout (no store).
 template <int ST, int KIND, bool ODD, bool MOM>
-__global__ void __launch_bounds__(kBX * kBY) aa_step_kernel(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_constant__ StepArgs a) {
   using T = typename Codec<ST>::T;
   constexpr int H = frame_of<KIND>();
   constexpr int SW = kBX + 2 * H, SH = kBY + 2 * H;

@@ -837,7 +837,8 @@ hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
   long long hdr[8] = {0x484c424d31LL, c->lattice, c->nx, c->ny, c->nz, c->storage, c->steps, 0};
   std::memcpy(host_buf, hdr, sizeof(hdr));
   const size_t pbytes = (size_t)c->Q * c->N * c->elem;
-  HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64, c->pop[c->cur], pbytes, cudaMemcpyDeviceToHost,
+  HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64, c->pop[c->aa ? 0 : c->cur], pbytes,
+                               cudaMemcpyDeviceToHost,
                                c->stream), "cudaMemcpyAsync");
   if (c->walls)   // the wall targets: the previous step's moments
     HLBM_CUDA(c, cudaMemcpyAsync(static_cast<char*>(host_buf) + 64 + pbytes, c->mom[c->cur], (size_t)16 * c->N,
