@@ -105,7 +105,7 @@ def _peaks():
 
 # the sources that define the 2D fused step kernels (what the DRAM counters describe)
 STEP2D_SOURCES = ("step2d.cuh", "step_common.cuh", "tma.cuh", "lattice.cuh", "lattice_gen.cpp", "internal.h",
-                  "step2d_f32.cu", "step2d_f16.cu", "step2d_bf16.cu")
+                  "step2d_f32.cu", "step2d_f16.cu", "step2d_bf16.cu", "aa.cu")
 
 
 def _kernel_source_hash() -> str:
@@ -134,10 +134,10 @@ def _launches(case, sched, steps) -> int:
     return -(-steps // smax)
 
 
-def _ncu_traffic(kernel_hash: str, storage: str, schedule):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if it was captured from the current kernel sources with this schedule;
-    else None."""
+def _ncu_traffic(kernel_hash: str, storage: str, schedule, workload: str = "thermal1024"):
+    """DRAM bytes per step of the fused kernel from the committed ncu summary
+    (a range capture over consecutive steps), if it was captured from the
+    current kernel sources on this workload with this schedule; else None."""
     p = ROOT / "profiles" / "fused_step_thermal1024_dram.json"
     if not p.exists():
         return None
@@ -148,7 +148,8 @@ def _ncu_traffic(kernel_hash: str, storage: str, schedule):
     if d.get("kernel_source_sha") != kernel_hash:
         return None
     for e in d.get("entries", []):
-        if e.get("storage") == storage and list(e.get("schedule", [])) == list(schedule):
+        if (e.get("storage") == storage and list(e.get("schedule", [])) == list(schedule)
+                and e.get("workload", "thermal1024") == workload):
             # multi-step entries: one launch runs several steps; the figure is per step
             return e.get("dram_bytes_per_step", e.get("dram_bytes_per_launch"))
     return None
@@ -735,7 +736,7 @@ def main():
                              (bytes_per_node // 2 * nodes // 2 ** 20)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": _ncu_traffic(khash, args.storage, sched),
+                         "traffic": _ncu_traffic(khash, args.storage, sched, args.workload),
                          "algorithmic_bytes_per_node": bytes_per_node,
                          "kernel": "aa_step_kernel (in place, one launch per step)" if case.params.get("lag") else
                                    (("step3d_rows_kernel" if sched[2] >= 2 and case.nx in (32, 64, 128, 256)
