@@ -288,6 +288,25 @@ int hlbm_lattice_info(int lattice, int* c, double* w, double* cs2);
 hlbm_status hlbm_population_sums_noalloc(int lattice, long long nodes, int storage, double rho0,
                                          const void* populations, void* cuda_stream, double* out);
 
+/* Bounds record of the debug build.  The library built with HLBM_DEBUG
+ * (libhlbm_debug.so) checks, before each access, every index of a wrapped
+ * global gather, of the shared-memory staging planes and neighbour frames,
+ * of every population store, every TMA box origin (inside the domain, on
+ * the 16-byte grid) and TMA shared-memory base (128-byte aligned) against
+ * its buffer; an index outside it is counted and the access goes to element
+ * 0 (loads) or is dropped (stores, copies: a dropped copy makes the bounded
+ * wait expire, HLBM_ETIMEOUT; a misaligned base ends the CTA).  No kernel
+ * reads or writes outside its buffers then, and no fault is raised.
+ *   out    host array of 4: number of rejected accesses since the last clear,
+ *          then site, index and bound of the first (site 1 gather, 2 staging
+ *          plane, 3 neighbour frame, 4 population store, 5 TMA box origin,
+ *          6 previous-step field, 7 TMA shared-memory base)
+ *   clear  nonzero: zero the record after reading it
+ * There is one record per device, shared by all contexts on it; the call
+ * reads the current device's record and synchronises the device first.  The
+ * release build returns HLBM_EUNSUPPORTED. */
+hlbm_status hlbm_debug_record(unsigned long long* out, int clear);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,15 +3,20 @@ include/hlbm.h, with the same names and argument order.  Argument marshalling
 only: every step of the computation runs in the library's CUDA kernels.
 
 Importing this module loads the in-tree library
-(paper_2411_10751_gb300/_build/libhlbm.so) and raises ImportError if it has
-not been built; there is no fallback implementation.
+(paper_2411_10751_gb300/_build/libhlbm.so; with the environment variable
+HLBM_LIBRARY=debug its bounds-checking variant _build/debug/libhlbm_debug.so)
+and raises ImportError if it has not been built; there is no fallback
+implementation.
 """
 from __future__ import annotations
 
 import ctypes as C
+import os
 from pathlib import Path
 
-LIB_PATH = Path(__file__).resolve().parent / "_build" / "libhlbm.so"
+_BUILD = Path(__file__).resolve().parent / "_build"
+DEBUG = os.environ.get("HLBM_LIBRARY", "") == "debug"
+LIB_PATH = _BUILD / "debug" / "libhlbm_debug.so" if DEBUG else _BUILD / "libhlbm.so"
 
 HLBM_D2Q37, HLBM_D3Q39 = 0, 1
 HLBM_F32, HLBM_F16, HLBM_BF16 = 0, 1, 2
@@ -27,7 +32,7 @@ EXPORTS = ["hlbm_workspace_bytes", "hlbm_create", "hlbm_bind_memory", "hlbm_set_
            "hlbm_save", "hlbm_load", "hlbm_step_count", "hlbm_set_tile", "hlbm_synchronize", "hlbm_set_wait_timeout",
            "hlbm_last_error", "hlbm_destroy", "hlbm_lattice_info", "hlbm_population_sums_noalloc",
            "hlbm_adjoint_workspace_bytes", "hlbm_adjoint_run", "hlbm_batch_create", "hlbm_batch_step",
-           "hlbm_batch_synchronize", "hlbm_batch_get_stream", "hlbm_batch_destroy"]
+           "hlbm_batch_synchronize", "hlbm_batch_get_stream", "hlbm_batch_destroy", "hlbm_debug_record"]
 
 
 class hlbm_source_params(C.Structure):
@@ -44,8 +49,8 @@ class HLBMError(RuntimeError):
 
 
 if not LIB_PATH.exists():
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2411_10751_gb300.build` "
-                      "(or __graft_entry__.build())")
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2411_10751_gb300.build"
+                      f"{' --debug' if DEBUG else ''}` (or __graft_entry__.build())")
 
 _lib = C.CDLL(str(LIB_PATH))
 
@@ -80,6 +85,7 @@ _sigs = {
     "hlbm_batch_synchronize": ([_vp], _i),
     "hlbm_batch_get_stream": ([_vp], _vp),
     "hlbm_batch_destroy": ([_vp], _i),
+    "hlbm_debug_record": ([C.POINTER(C.c_ulonglong), _i], _i),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -97,3 +103,11 @@ def check(status: int, ctx=None) -> None:
 
 def library_path() -> str:
     return str(LIB_PATH)
+
+
+def debug_record(clear: bool = True):
+    """The debug library's bounds record: (count, site, index, bound) of the
+    first rejected access on the current device (zeros: none)."""
+    out = (C.c_ulonglong * 4)()
+    check(hlbm_debug_record(out, int(clear)))
+    return tuple(int(v) for v in out)

@@ -3,7 +3,9 @@
 Steps: compile and run the host generator of the D2Q37 quadrature weights
 (csrc/lattice_gen.cpp -> _build/lattice_weights.inc), compile every CUDA
 translation unit in parallel with nvcc, link a shared library.  Output:
-paper_2411_10751_gb300/_build/libhlbm.so.
+paper_2411_10751_gb300/_build/libhlbm.so; with debug=True (`--debug`) the
+bounds-checking variant _build/debug/libhlbm_debug.so, which the binding
+loads instead when HLBM_LIBRARY=debug is set.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libhlbm.so"
+DEBUG_LIB = BUILD / "debug" / "libhlbm_debug.so"
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,7 +46,9 @@ def _stale(target: Path, deps) -> bool:
     return any(d.stat().st_mtime > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> Path:
+    """debug: the bounds-checking variant (HLBM_DEBUG) as
+    _build/debug/libhlbm_debug.so."""
     BUILD.mkdir(exist_ok=True)
     gen = BUILD / "lattice_gen"
     inc = BUILD / "lattice_weights.inc"
@@ -52,21 +57,25 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     if force or _stale(inc, [gen]):
         _run([str(gen), str(inc)])
     headers = list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + [ROOT / "include" / "hlbm.h", inc]
+    out_dir, lib, extra = BUILD, LIB, []
+    if debug:
+        out_dir, lib, extra = DEBUG_LIB.parent, DEBUG_LIB, ["-DHLBM_DEBUG"]
+        out_dir.mkdir(exist_ok=True)
     objs, jobs = [], []
     for cu in sources():
-        obj = BUILD / (cu.stem + ".o")
+        obj = out_dir / (cu.stem + ".o")
         objs.append(obj)
         if force or _stale(obj, [cu] + headers):
-            jobs.append([NVCC, *ARCH, *CFLAGS, "-c", str(cu), "-o", str(obj)])
+            jobs.append([NVCC, *ARCH, *CFLAGS, *extra, "-c", str(cu), "-o", str(obj)])
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for r in ex.map(_run, jobs):
                 if verbose and r.stderr:
                     print(r.stderr, file=sys.stderr)
-    if force or jobs or _stale(LIB, objs):
-        _run([NVCC, *ARCH, "-shared", "-o", str(LIB), *map(str, objs)])
-    return LIB
+    if force or jobs or _stale(lib, objs):
+        _run([NVCC, *ARCH, "-shared", "-o", str(lib), *map(str, objs)])
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

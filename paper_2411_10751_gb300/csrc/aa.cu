@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_cons
     for (int k = tid; k < SW * SH; k += kBX * kBY) {
       const int j = k / SW, i = k - j * SW;
       const int X = wrapm(x0 - H + i, nx), Y = wrapm(y0 - H + j, ny);
-      aux[k] = __ldg(a.aux_rd + (size_t)Y * nx + X);
+      aux[k] = __ldg(a.aux_rd + HLBM_IDX((long long)Y * nx + X, a.N, DBG_AUX));
     }
     __syncthreads();
   }
@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_cons
   static_for<37>([&](auto I) {
     constexpr int i = I;
     if constexpr (!ODD) {
-      g[i] = to_float(f[(size_t)i * N + (size_t)yc * nx + xc]);
+      g[i] = to_float(f[HLBM_IDX((long long)i * N + (long long)yc * nx + xc, 37 * a.N, DBG_GATHER)]);
     } else {
       constexpr int cx = L::c(i, 0), cy = L::c(i, 1), b = aa_opp(i);
-      g[i] = to_float(f[(size_t)b * N + ys[cy + 3] + xs[cx + 3]]);
+      g[i] = to_float(f[HLBM_IDX((long long)b * N + ys[cy + 3] + xs[cx + 3], 37 * a.N, DBG_GATHER)]);
     }
   });
   const int node = yc * nx + xc;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_cons
     }
     return;
   } else {
-    if (!active) return;
+    if (!active || !HLBM_IN(node, a.N, DBG_STORE)) return;
     // this step's field for the next step's neighbours
     if constexpr (KIND == KIND_SC) a.aux_wr[node] = psi_now;
     if constexpr (KIND == KIND_THERMAL) a.aux_wr[node] = tb;
@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_cons
         fo[(size_t)b * N + node] = v;                             // slot ibar of x
       } else {
         constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
-        fo[(size_t)i * N + ys[3 - cy] + xs[3 - cx]] = v;          // slot i of x + c_i
+        const long long o = (long long)i * N + ys[3 - cy] + xs[3 - cx];
+        if (HLBM_IN(o, 37 * a.N, DBG_STORE)) fo[o] = v;           // slot i of x + c_i
       }
     });
   }

@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(256, 2)
   const int ntiles = nty * nz;
   const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
   const int tid = threadIdx.x, xm = nx - 1;
+  if (!HLBM_IN(smem_u32(smem) & 127u, 1, DBG_SMEM)) return;   // TMA destinations need 128-byte alignment
   const int xk = tid & xm, rk = tid / nx;
   const bool isf = tid < L::Q, isl = tid >= 128 && tid < 128 + L::Q, isg = tid >= 64 && tid < 67;
   const int p = isf ? tid : (isl ? tid - 128 : tid - 64);   // the plane this thread copies
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(256, 2)
     }
     t = tn;
   }
-  if (tid == RED) bulk_wait_all();
+  if (tid == RED) bulk_wait_read_all();   // the reductions have read their source; they complete with the grid
 }
 
 // Whether the whole-row kernel serves this domain (rows of the stored type

@@ -551,6 +551,7 @@ size_t hlbm_workspace_bytes(int lattice, int nx, int ny, int nz, const hlbm_sour
 
 hlbm_status hlbm_create(int lattice, int nx, int ny, int nz, double tau_hat, const hlbm_source_params* p,
                         hlbm_ctx** out) {
+  NvtxRange range("hlbm_create");
   if (!out) return HLBM_EINVAL;
   *out = nullptr;
   std::string why;
@@ -618,6 +619,7 @@ void* hlbm_get_stream(hlbm_ctx* c) {
 }
 
 hlbm_status hlbm_init(hlbm_ctx* c, const float* rho, const float* u, const float* theta, int on_device) {
+  NvtxRange range("hlbm_init");
   if (!c || !rho || !u || !theta) return HLBM_EINVAL;
   hlbm_status st = ensure_memory(c);
   if (st != HLBM_OK) return st;
@@ -696,6 +698,7 @@ hlbm_status hlbm_set_force_field(hlbm_ctx* c, const float* g, int kind, int on_d
 }
 
 hlbm_status hlbm_step(hlbm_ctx* c, int n) {
+  NvtxRange range("hlbm_step");
   hlbm_status st = usable(c);
   if (st != HLBM_OK) return st;
   if (n < 0) return fail(c, HLBM_EINVAL, "n must be >= 0");
@@ -707,6 +710,7 @@ hlbm_status hlbm_step(hlbm_ctx* c, int n) {
   }
   if (multistep_ok(c)) {
     while (n > 0) {
+      NvtxRange chunk("hlbm_step: multi-step launch");
       const int S = std::min(n, multistep_max(c));
       HLBM_CUDA(c, launch_multistep(c, S), "multi-step kernel");
       n -= S;
@@ -714,8 +718,10 @@ hlbm_status hlbm_step(hlbm_ctx* c, int n) {
     return HLBM_OK;
   }
   while (n >= kGraphSteps) {
+    NvtxRange chunk("hlbm_step: graph of 32 steps");
     cudaGraphExec_t& ge = c->graph[c->cur];
     if (!ge) {
+      NvtxRange capture("hlbm_step: capture and instantiate");
       const int cur0 = c->cur;
       HLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
       cudaError_t le = cudaSuccess;
@@ -736,15 +742,19 @@ hlbm_status hlbm_step(hlbm_ctx* c, int n) {
     n -= kGraphSteps;
     c->steps += kGraphSteps;
   }
-  for (int k = 0; k < n; ++k) {
-    cudaError_t e = one_step(c);
-    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
-    c->steps += 1;
+  if (n > 0) {
+    NvtxRange chunk("hlbm_step: single launches");
+    for (int k = 0; k < n; ++k) {
+      cudaError_t e = one_step(c);
+      if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+      c->steps += 1;
+    }
   }
   return HLBM_OK;
 }
 
 hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on_device) {
+  NvtxRange range("hlbm_moments");
   hlbm_status st = usable(c);
   if (st != HLBM_OK) return st;
   if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
@@ -789,6 +799,7 @@ hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on
 }
 
 hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
+  NvtxRange range("hlbm_diag");
   hlbm_status st = usable(c);
   if (st != HLBM_OK) return st;
   if (!out) return HLBM_EINVAL;
@@ -830,6 +841,7 @@ size_t hlbm_state_bytes(const hlbm_ctx* c) {
 }
 
 hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
+  NvtxRange range("hlbm_save");
   hlbm_status st = usable(c);
   if (st != HLBM_OK) return st;
   if (!host_buf || bytes < hlbm_state_bytes(c)) return fail(c, HLBM_EINVAL, "buffer too small");
@@ -851,6 +863,7 @@ hlbm_status hlbm_save(hlbm_ctx* c, void* host_buf, size_t bytes) {
 }
 
 hlbm_status hlbm_load(hlbm_ctx* c, const void* host_buf, size_t bytes) {
+  NvtxRange range("hlbm_load");
   if (!c || !host_buf) return HLBM_EINVAL;
   if (bytes < hlbm_state_bytes(c)) return fail(c, HLBM_EINVAL, "buffer too small");
   long long hdr[8];
@@ -959,6 +972,7 @@ size_t hlbm_adjoint_workspace_bytes(const hlbm_ctx* c, int steps, int ckpt_every
 
 hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* workspace, size_t bytes, float* dLdg,
                              double* loss) {
+  NvtxRange range("hlbm_adjoint_run");
   hlbm_status st = usable(c);
   if (st != HLBM_OK) return st;
   if (!c->initialised) return fail(c, HLBM_ESTATE, "hlbm_init has not been called");
@@ -994,23 +1008,26 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   // after hlbm_step), so there is neither a checkpoint copy nor a recompute
   const int cur0 = c->cur;
   auto slot = [&](int k) -> void* { return k == 0 ? c->pop[cur0] : (k == steps ? c->pop[cur0 ^ 1] : state(k)); };
-  if (K == 1) {
-    for (int k = 0; k < steps; ++k) {
-      StepArgs a = make_args(c);
-      a.fin = slot(k);
-      a.fout = slot(k + 1);
-      a.reverse = k & 1;
-      HLBM_CUDA(c, launch_step(c, a, false), "forward step");
-    }
-    c->cur = cur0 ^ 1;
-    c->steps += steps;
-  } else {
-    for (int k = 0; k < nseg; ++k) {
-      HLBM_CUDA(c, cudaMemcpyAsync(state(k), c->pop[c->cur], sbytes, cudaMemcpyDeviceToDevice, c->stream),
-                "checkpoint");
-      const int len = std::min(K, steps - k * K);
-      for (int j = 0; j < len; ++j) HLBM_CUDA(c, one_step(c), "forward step");
-      c->steps += len;
+  {
+    NvtxRange fwd("adjoint: forward sweep with checkpoints");
+    if (K == 1) {
+      for (int k = 0; k < steps; ++k) {
+        StepArgs a = make_args(c);
+        a.fin = slot(k);
+        a.fout = slot(k + 1);
+        a.reverse = k & 1;
+        HLBM_CUDA(c, launch_step(c, a, false), "forward step");
+      }
+      c->cur = cur0 ^ 1;
+      c->steps += steps;
+    } else {
+      for (int k = 0; k < nseg; ++k) {
+        HLBM_CUDA(c, cudaMemcpyAsync(state(k), c->pop[c->cur], sbytes, cudaMemcpyDeviceToDevice, c->stream),
+                  "checkpoint");
+        const int len = std::min(K, steps - k * K);
+        for (int j = 0; j < len; ++j) HLBM_CUDA(c, one_step(c), "forward step");
+        c->steps += len;
+      }
     }
   }
   // seed from the final state: lambda_T, dL/dg at T, kinetic energy
@@ -1045,6 +1062,7 @@ hlbm_status hlbm_adjoint_run(hlbm_ctx* c, int steps, int ckpt_every, void* works
   int cur = 0;
   // backward over segments: recompute the segment's states, then reverse steps
   for (int k = nseg - 1; k >= 0; --k) {
+    NvtxRange segment("adjoint: segment (recompute, reverse steps)");
     const int len = std::min(K, steps - k * K);
     // states of the segment: j = 0 is checkpoint k, j >= 1 are recomputed into slots nseg + j - 1
     auto seg = [&](int j) { return j == 0 ? (K == 1 ? slot(k) : state(k)) : state((size_t)nseg + j - 1); };
@@ -1088,6 +1106,18 @@ int hlbm_lattice_info(int lattice, int* cvec, double* w, double* cs2) {
     return 39;
   }
   return 0;
+}
+
+hlbm_status hlbm_debug_record(unsigned long long* out, int clear) {
+#ifdef HLBM_DEBUG
+  if (!out) return HLBM_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return HLBM_ECUDA;
+  return debug_record(out, clear != 0) ? HLBM_OK : HLBM_ECUDA;
+#else
+  (void)out;
+  (void)clear;
+  return HLBM_EUNSUPPORTED;
+#endif
 }
 
 }  // extern "C"

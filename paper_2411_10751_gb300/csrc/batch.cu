@@ -64,7 +64,10 @@ __device__ __forceinline__ bool batch_tile(const BatchDomain& dom, const StepArg
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + batch_smem<ST>() - 128);
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (dom.has_map && tile_boxed<Cf>(a, x0, y0) && ((smem_u32(smem) & 127u) == 0)) {
-    if (tid == 0) issue_tile<Cf>(sp, &dom.tmap[par], bar, x0, y0, a.debug_skip_tma);
+    if (tid == 0) {
+      fence_proxy_async_smem();   // the previous tile's generic accesses of the buffer come first
+      issue_tile<Cf>(sp, &dom.tmap[par], bar, x0, y0, a.debug_skip_tma, a.nx, a.ny);
+    }
     const bool ok = mbar_wait_bounded(bar, phase, a.wait_ns);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) {
@@ -95,14 +98,22 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ int s_item;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + batch_smem<ST>() - 128);
+  // thread 0 takes the counter one item ahead and keeps the raw value until
+  // the next item starts, so the atomic's round trip overlaps a whole tile
+  unsigned long long nxt_raw = 0;
+  const unsigned long long period = (unsigned long long)nitems + gridDim.x;
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    nxt_raw = atomicAdd(ctr, 1ull);
   }
   uint32_t phase = 0;
-  const unsigned long long period = (unsigned long long)nitems + gridDim.x;
   for (;;) {
-    if (tid == 0) s_item = (int)(atomicAdd(ctr, 1ull) % period);
+    if (tid == 0) {
+      const int gi = (int)(nxt_raw % period);
+      s_item = gi;
+      if (gi < nitems) nxt_raw = atomicAdd(ctr, 1ull);
+    }
     __syncthreads();
     const int gi = s_item;
     if (gi >= nitems) break;
@@ -307,6 +318,7 @@ static cudaError_t batch_launch(hlbm_batch* b, int flip) {
 }
 
 hlbm_status hlbm_batch_step(hlbm_batch* b, int n) {
+  NvtxRange range("hlbm_batch_step");
   if (!b || n < 0) return HLBM_EINVAL;
   if (n == 0) return HLBM_OK;
   hlbm_status st = batch_refresh(b);

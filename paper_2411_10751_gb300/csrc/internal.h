@@ -4,10 +4,22 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cstdint>
 
 namespace hlbm {
+
+// NVTX range over a host scope (entry points, step chunks, adjoint sweeps and
+// segments), shown on the timeline by Nsight Systems and usable as an ncu
+// range filter; without an attached tool a push or pop is one test of an
+// unset function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // A per-device value (a kernel's resident-CTA count) computed once per device:
 // compute(dev) runs on the first call with that device current; concurrent
@@ -175,5 +187,11 @@ cudaError_t launch_adjoint(int lattice, int storage, bool seed, const void* fwd,
                            const float* gfield, float* dLdg, double* partials, long long N, int nx, int ny, int nz,
                            float rho0, float omega, float beta, int thermal, const AdjRows& rows, cudaStream_t s);
 int adjoint_seed_blocks(long long N);
+
+// debug build only (kernels_misc.cu): the records of rejected indices of all
+// translation units, summed (count) and the first non-empty one's site,
+// index and bound; each unit registers the reader of its own record
+bool debug_record(unsigned long long* out, bool clear);
+bool dbg_register(bool (*reader)(unsigned long long*, bool));
 
 }  // namespace hlbm

@@ -3,6 +3,9 @@
 // lattice and storage.
 #include "step_common.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace hlbm {
 
 cudaError_t launch_step2d_f32(const StepArgs&, int, bool, int, int, const CUtensorMap*, cudaStream_t);
@@ -28,15 +31,57 @@ cudaError_t launch_step_d2q37(const StepArgs& a, int kind, int storage, bool mom
   return cudaErrorInvalidValue;
 }
 
+// Kernel attributes (dynamic shared memory) belong to the device's context:
+// set once per device and storage (concurrent first calls set them twice,
+// which is harmless).
 cudaError_t configure_step_d2q37(int storage) {
-  static bool done[3] = {false, false, false};
+  static std::atomic<int> done[3][kMaxDevicesCached];
   if (storage < 0 || storage > 2) return cudaErrorInvalidValue;
-  if (done[storage]) return cudaSuccess;
-  cudaError_t e = storage == ST_F32   ? configure_step2d_f32()
-                  : storage == ST_F16 ? configure_step2d_f16()
-                                      : configure_step2d_bf16();
-  if (e == cudaSuccess) done[storage] = true;
+  cudaError_t e = cudaSuccess;
+  per_device_cached(done[storage], [&](int) {
+    e = storage == ST_F32   ? configure_step2d_f32()
+        : storage == ST_F16 ? configure_step2d_f16()
+                            : configure_step2d_bf16();
+    return e == cudaSuccess ? 1 : 0;
+  });
   return e;
+}
+
+namespace {
+std::vector<bool (*)(unsigned long long*, bool)>& dbg_readers() {
+  static std::vector<bool (*)(unsigned long long*, bool)> r;
+  return r;
+}
+std::mutex& dbg_mutex() {
+  static std::mutex m;
+  return m;
+}
+}  // namespace
+
+bool dbg_register(bool (*reader)(unsigned long long*, bool)) {
+  std::lock_guard<std::mutex> lock(dbg_mutex());
+  dbg_readers().push_back(reader);
+  return true;
+}
+
+// The debug build's records of rejected indices (step_common.cuh): summed
+// count and the first non-empty record, optionally cleared; false in the
+// release build (no unit registers a reader there).
+bool debug_record(unsigned long long* out, bool clear) {
+  std::lock_guard<std::mutex> lock(dbg_mutex());
+  if (dbg_readers().empty()) return false;
+  out[0] = out[1] = out[2] = out[3] = 0;
+  for (auto* rd : dbg_readers()) {
+    unsigned long long r[4];
+    if (!rd(r, clear)) return false;
+    if (r[0] && !out[0]) {
+      out[1] = r[1];
+      out[2] = r[2];
+      out[3] = r[3];
+    }
+    out[0] += r[0];
+  }
+  return true;
 }
 
 void step_box_d2q37(int kind, int storage, bool mom, int rows, int* wb, int* hb, int* ob) {

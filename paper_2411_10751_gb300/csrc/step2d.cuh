@@ -77,13 +77,24 @@ struct Frame2 {
   }
 };
 
+// Index of population i at in-box offset off in the staged planes, and of
+// frame entry k (both checked against their extent in the debug build).
+template <class Cf>
+__device__ __forceinline__ int stg(int i, int off) {
+  return i * Cf::PLANE + HLBM_IDX(off, Cf::WB * Cf::HB, DBG_STAGE);
+}
+template <class Fr>
+__device__ __forceinline__ int frm(int k) {
+  return HLBM_IDX(k, Fr::SW * Fr::SH, DBG_FRAME);
+}
+
 // the Q pulled populations of region node (rx, ry) from the staged planes
 template <class Cf>
 __device__ __forceinline__ void load_region(const typename Cf::T* sp, int rx, int ry, float (&g)[37]) {
   const int base = ry * Cf::WB + rx;
   static_for<37>([&](auto I) {
     constexpr int i = I;
-    g[i] = to_float(sp[i * Cf::PLANE + base + Cf::rem(i)]);
+    g[i] = to_float(sp[stg<Cf>(i, base + Cf::rem(i))]);
   });
 }
 
@@ -116,14 +127,22 @@ constexpr int min_ctas2() {
 // Issues the Q staging boxes of the tile at (x0, y0) against `bar`.
 template <class Cf>
 __device__ __forceinline__ void issue_tile(typename Cf::T* sp, const CUtensorMap* tmap, uint64_t* bar, int x0, int y0,
-                                           int skip) {
+                                           int skip, int nx, int ny) {
   using L = D2Q37;
   constexpr int H = Cf::H;
   mbar_arrive_expect_tx(bar, Cf::TX_BYTES);
   if (!skip) {
     static_for<37>([&](auto I) {
       constexpr int i = I;
-      tma_load_3d(sp + i * Cf::PLANE, tmap, x0 - H - L::c(i, 0) - Cf::rem(i), y0 - H - L::c(i, 1), i, bar);
+      const int bx = x0 - H - L::c(i, 0) - Cf::rem(i), by = y0 - H - L::c(i, 1);
+#ifdef HLBM_DEBUG
+      // the box must start on the 16-byte grid and lie inside the domain
+      // (a dropped box leaves the barrier short: the bounded wait expires)
+      if (!HLBM_IN(bx % Cf::A, 1, DBG_BOX) || !HLBM_IN(bx, nx - Cf::WB + 1, DBG_BOX) ||
+          !HLBM_IN(by, ny - Cf::HB + 1, DBG_BOX))
+        return;
+#endif
+      tma_load_3d(sp + i * Cf::PLANE, tmap, bx, by, i, bar);
     });
   }
 }
@@ -154,7 +173,7 @@ __device__ __forceinline__ void fill_tile_wrapped(const StepArgs& a, const void*
     const int base = ry * Cf::WB + rx;
     static_for<37>([&](auto I) {
       constexpr int i = I;
-      sp[i * Cf::PLANE + base + Cf::rem(i)] = from_float<T>(gk[i]);
+      sp[stg<Cf>(i, base + Cf::rem(i))] = from_float<T>(gk[i]);
     });
   }
 }
@@ -200,7 +219,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
     constexpr int i = I;
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-      set_lane(g[i], k, to_float(sp[i * Cf::PLANE + (ty + k * TR + H) * Cf::WB + tx + H + Cf::rem(i)]));
+      set_lane(g[i], k, to_float(sp[stg<Cf>(i, (ty + k * TR + H) * Cf::WB + tx + H + Cf::rem(i))]));
   });
   V dr, dr_l, acc, J[3], Pih;
   moments_h<L>(g, dr, dr_l, acc, J, Pih);
@@ -221,7 +240,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
       set_lane(psi, k, psi_of<L>(a, lane(dr, k), lane(dr_l, k)));
-      aux[(ty + k * TR + H) * Fr::SW + tx + H] = lane(psi, k);
+      aux[frm<Fr>((ty + k * TR + H) * Fr::SW + tx + H)] = lane(psi, k);
     }
     for (int k = tid; k < Fr::count; k += NT) {
       int i, j;
@@ -229,11 +248,11 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
       float gh[37];
       static_for<37>([&](auto I) {
         constexpr int q = I;
-        gh[q] = to_float(sp[q * Cf::PLANE + j * Cf::WB + i + Cf::rem(q)]);
+        gh[q] = to_float(sp[stg<Cf>(q, j * Cf::WB + i + Cf::rem(q))]);
       });
       float hl;
       const float hd = density_h<L>(gh, hl);
-      aux[j * Fr::SW + i] = psi_of<L>(a, hd, hl);
+      aux[frm<Fr>(j * Fr::SW + i)] = psi_of<L>(a, hd, hl);
     }
     __syncthreads();
     staged_done();
@@ -246,7 +265,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
 #pragma unroll
       for (int k = 0; k < NPT; ++k) {
         const int r = ty + k * TR + H;
-        set_lane(dpsi, k, aux[(r + cy) * Fr::SW + tx + H + cx] - aux[(r - cy) * Fr::SW + tx + H - cx]);
+        set_lane(dpsi, k, aux[frm<Fr>((r + cy) * Fr::SW + tx + H + cx)] - aux[frm<Fr>((r - cy) * Fr::SW + tx + H - cx)]);
       }
       if constexpr (cx != 0) sx = vfma(splat<V>((float)(L::w(i) * cx)), dpsi, sx);
       if constexpr (cy != 0) sy = vfma(splat<V>((float)(L::w(i) * cy)), dpsi, sy);
@@ -314,7 +333,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
     if constexpr (KIND == KIND_THERMAL) {
       // theta - 1 on the tile and its 4-neighbour ring, then grad theta
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) aux[(ty + k * TR + 1) * Fr::SW + tx + 1] = lane(tb_m, k);
+      for (int k = 0; k < NPT; ++k) aux[frm<Fr>((ty + k * TR + 1) * Fr::SW + tx + 1)] = lane(tb_m, k);
       for (int k = tid; k < Fr::count; k += NT) {
         int i, j;
         Fr::pos(k, i, j);
@@ -322,9 +341,9 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
         float gh[37];
         static_for<37>([&](auto I) {
           constexpr int q = I;
-          gh[q] = to_float(sp[q * Cf::PLANE + j * Cf::WB + i + Cf::rem(q)]);
+          gh[q] = to_float(sp[stg<Cf>(q, j * Cf::WB + i + Cf::rem(q))]);
         });
-        aux[j * Fr::SW + i] = theta_bar_local<L>(a, gh, hy * nx + hx, hy);
+        aux[frm<Fr>(j * Fr::SW + i)] = theta_bar_local<L>(a, gh, hy * nx + hx, hy);
       }
       __syncthreads();
       staged_done();
@@ -332,8 +351,8 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
 #pragma unroll
       for (int k = 0; k < NPT; ++k) {
         const int r = ty + k * TR + 1;
-        set_lane(gtx, k, 0.5f * (aux[r * Fr::SW + tx + 2] - aux[r * Fr::SW + tx]));
-        set_lane(gty, k, 0.5f * (aux[(r + 1) * Fr::SW + tx + 1] - aux[(r - 1) * Fr::SW + tx + 1]));
+        set_lane(gtx, k, 0.5f * (aux[frm<Fr>(r * Fr::SW + tx + 2)] - aux[frm<Fr>(r * Fr::SW + tx)]));
+        set_lane(gty, k, 0.5f * (aux[frm<Fr>((r + 1) * Fr::SW + tx + 1)] - aux[frm<Fr>((r - 1) * Fr::SW + tx + 1)]));
       }
       // s^(3) += rho theta (1 - 1/Pr) [delta grad_xi theta], grad_xi = c0 grad
       const V hc = vmul(vmul(rho, vadd(splat<V>(1.f), tb_m)), splat<V>(a.h_coef * (float)L::c0));
@@ -370,7 +389,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
         constexpr int i = I;
 #pragma unroll
         for (int k = 0; k < NPT; ++k)
-          sp[i * Cf::PLANE + (ty + k * TR) * BX + tx] = round_store<T>(lane(g[i], k), pop_bits(salt[k], i));
+          sp[stg<Cf>(i, (ty + k * TR) * BX + tx)] = round_store<T>(lane(g[i], k), pop_bits(salt[k], i));
       });
       fence_proxy_async_smem();
       __syncthreads();
@@ -380,12 +399,12 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
           tma_store_3d(tmap_out, sp + i * Cf::PLANE, x0, y0, i);
         });
         bulk_commit();
-        bulk_wait_all();
+        bulk_wait_read_all();   // the staging buffer has been read; the writes complete with the grid
       }
     } else {
 #pragma unroll
       for (int k = 0; k < NPT; ++k) {
-        if (!activek[k]) continue;
+        if (!activek[k] || !HLBM_IN(nodek[k], a.N, DBG_STORE)) continue;
         T* __restrict__ fout = static_cast<T*>(fout_v) + nodek[k];
         static_for<37>([&](auto I) {
           constexpr int i = I;
@@ -414,7 +433,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, MOM, BY, N
       fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) issue_tile<Cf>(sp, &tmap, bar, x0, y0, a.debug_skip_tma);
+    if (tid == 0) issue_tile<Cf>(sp, &tmap, bar, x0, y0, a.debug_skip_tma, a.nx, a.ny);
     const bool ok = mbar_wait_bounded(bar, 0, a.wait_ns);
     if (!__syncthreads_and(ok)) {
       // copies did not complete: report, give in-flight copies a second bounded
@@ -535,10 +554,12 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
   // tid 0 takes tile indices one tile ahead, so that the counter's round
   // trip is not on the path to the next tile's copies: at staged_done it
   // stages the index taken during the previous tile and only then takes the
-  // next one.  Once it has taken an index >= T it takes no more, so a launch
-  // still takes exactly T + G values.
-  int nxt = 0;
-  auto take = [&]() { return (int)(atomicAdd(a.tile_ctr, 1ull) % period); };
+  // next one.  It keeps the counter's raw value until that next use: reducing
+  // it at once would stall thread 0 there for the atomic's round trip, and
+  // the whole CTA behind it at the tile's last barrier.  Once it has taken an
+  // index >= T it takes no more, so a launch still takes exactly T + G values.
+  unsigned long long nxt_raw = 0;
+  auto take = [&]() { return atomicAdd(a.tile_ctr, 1ull); };
   auto stage = [&](int tn) {   // tid 0: publishes tile tn and, if it is a boxed tile, stages it
     s_next = tn;
     if (tn < ntiles) {
@@ -546,21 +567,20 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       origin(tn, xn, yn);
       if (aligned && tile_boxed<Cf>(a, xn, yn)) {
         fence_proxy_async_smem();
-        issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma);
+        issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma, a.nx, a.ny);
       }
     }
   };
   auto take_and_issue = [&]() {
-    const int tn = nxt;
+    const int tn = (int)(nxt_raw % period);
     stage(tn);
-    if (tn < ntiles) nxt = take();
+    if (tn < ntiles) nxt_raw = take();
   };
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
-    const int t0 = take();
-    stage(t0);
-    nxt = (t0 < ntiles) ? take() : t0;
+    nxt_raw = take();
+    take_and_issue();
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -665,7 +685,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
     if (aligned && tile_boxed<Cf>(a, tx * 32, ty * BY)) {
       fence_proxy_async_global();   // the acquired generic-proxy writes before these bulk reads
       fence_proxy_async_smem();
-      issue_tile<Cf>(sp, (s & 1) ? &tm_odd : &tm_even, bar, tx * 32, ty * BY, a.debug_skip_tma);
+      issue_tile<Cf>(sp, (s & 1) ? &tm_odd : &tm_even, bar, tx * 32, ty * BY, a.debug_skip_tma, a.nx, a.ny);
     }
   };
   // tid 0 at staged_done: takes the tile after next, releases the previous

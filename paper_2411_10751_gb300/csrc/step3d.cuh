@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas3<MOM, NPT>()))
     T* __restrict__ fout = static_cast<T*>(a.fout);
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
-      if (!activek[k]) continue;
+      if (!activek[k] || !HLBM_IN(nodek[k], a.N, DBG_STORE)) continue;
       // 16-bit storage: stochastic rounding keyed by node and result (step_common.cuh)
       const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(nodek[k], lane(g[0], k));
       static_for<L::Q>([&](auto I) {
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(128, 3)
   const int ntiles = nty * nz;
   const unsigned long long period = (unsigned long long)ntiles + gridDim.x;
   const int tid = threadIdx.x, xm = nx - 1;
+  if (!HLBM_IN(smem_u32(smem) & 127u, 1, DBG_SMEM)) return;   // TMA destinations need 128-byte alignment
   int xk[2], rk[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(128, 3)
     }
     const int zz = wrap_near3(z - pcz, nz);
     const int ys = y0 - pcy;
+    if (!HLBM_IN(zz, nz, DBG_BOX)) return;   // a dropped copy leaves the barrier short
     fence_proxy_async_smem();
     if (ys >= 0 && ys + by <= ny) {
       tma_load_4d(sp + tid * TN, &tm_box, 0, ys, zz, tid, bar);
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(128, 3)
       constexpr int i = I;
       constexpr int cx = L::c(i, 0);
 #pragma unroll
-      for (int k = 0; k < 2; ++k) set_lane(g[i], k, to_float(sp[i * TN + rk[k] * nx + ((xk[k] - cx) & xm)]));
+      for (int k = 0; k < 2; ++k) set_lane(g[i], k, to_float(sp[i * TN + HLBM_IDX(rk[k] * nx + ((xk[k] - cx) & xm), TN, DBG_STAGE)]));
     });
     __syncthreads();  // the staging buffer is free and the next index is published
     const int tn = s_next[it & 1];
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(128, 3)
     T* __restrict__ fout = static_cast<T*>(a.fout);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      if (!activek[k]) continue;
+      if (!activek[k] || !HLBM_IN(nodek[k], a.N, DBG_STORE)) continue;
       const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(nodek[k], lane(g[0], k));
       static_for<L::Q>([&](auto I) {
         constexpr int i = I;

@@ -39,6 +39,55 @@
 
 namespace hlbm {
 
+// ------------------------------------------------------------- debug build
+// Built with -DHLBM_DEBUG (a separate library), every gathered global index,
+// staged shared-memory index, neighbour-frame index, population store, TMA box
+// origin and TMA shared-memory destination is checked before the access.  An
+// index outside its buffer is counted in the device record dbg_record
+// ({count, site, index, bound} of the first; one record per translation unit,
+// which registers a host reader for it) and the access is redirected to
+// element 0 (loads) or dropped (stores and copies), so a faulty launch runs to
+// its end without touching memory outside its buffers, and the host reads the
+// records (hlbm_debug_record).  In the release build each check is the plain
+// index.
+enum DbgSite {
+  DBG_GATHER = 1,   // wrapped global gather of the pulled populations
+  DBG_STAGE = 2,    // staged populations in shared memory (reads and writes)
+  DBG_FRAME = 3,    // neighbour-field frame in shared memory
+  DBG_STORE = 4,    // global population store
+  DBG_BOX = 5,      // TMA box origin outside the domain or off the 16-byte grid
+  DBG_AUX = 6,      // neighbour fields and moments of the previous step (global)
+  DBG_SMEM = 7,     // shared-memory base of a TMA destination not 128-byte aligned
+};
+#ifdef HLBM_DEBUG
+static __device__ unsigned long long dbg_record[4];
+namespace {
+bool dbg_read_record(unsigned long long* out, bool clear) {
+  if (cudaMemcpyFromSymbol(out, dbg_record, 4 * sizeof(unsigned long long)) != cudaSuccess) return false;
+  const unsigned long long zero[4] = {0, 0, 0, 0};
+  return !clear || cudaMemcpyToSymbol(dbg_record, zero, sizeof(zero)) == cudaSuccess;
+}
+const bool dbg_registered = dbg_register(&dbg_read_record);
+}  // namespace
+static __device__ __noinline__ void dbg_reject(long long i, long long n, int site) {
+  if (atomicAdd(&dbg_record[0], 1ull) == 0ull) {
+    dbg_record[1] = (unsigned long long)site;
+    dbg_record[2] = (unsigned long long)i;
+    dbg_record[3] = (unsigned long long)n;
+  }
+}
+__device__ __forceinline__ bool dbg_ok(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  dbg_reject(i, n, site);
+  return false;
+}
+#define HLBM_IDX(i, n, site) (::hlbm::dbg_ok((long long)(i), (long long)(n), (site)) ? (i) : 0)
+#define HLBM_IN(i, n, site) ::hlbm::dbg_ok((long long)(i), (long long)(n), (site))
+#else
+#define HLBM_IDX(i, n, site) (i)
+#define HLBM_IN(i, n, site) true
+#endif
+
 // ------------------------------------------------------------------ codecs
 template <int S> struct Codec;
 template <> struct Codec<ST_F32> {
@@ -221,7 +270,7 @@ __device__ __forceinline__ void gather(const typename C::T* __restrict__ f, long
     constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     int off = ys[cy + 3] + xs[cx + 3];
     if constexpr (L::D == 3) off += zs[cz + 3];
-    g[i] = C::ld(f + (size_t)i * (size_t)N + off);
+    g[i] = C::ld(f + HLBM_IDX((size_t)i * (size_t)N + off, (long long)L::Q * N, DBG_GATHER));
   });
 }
 

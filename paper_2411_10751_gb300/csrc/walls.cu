@@ -104,7 +104,8 @@ __device__ __forceinline__ double peq_m1(double ux, double uy, double tb) {
 template <int ST>
 __device__ __forceinline__ float ldpop(const WallArgs& a, int i, int x, int y) {
   using T = typename Codec<ST>::T;
-  return Codec<ST>::ld(static_cast<const T*>(a.fin) + (size_t)i * (size_t)a.N + (size_t)y * a.nx + x);
+  return Codec<ST>::ld(static_cast<const T*>(a.fin) +
+                       HLBM_IDX((long long)i * a.N + (long long)y * a.nx + x, 37 * a.N, DBG_GATHER));
 }
 
 __device__ __forceinline__ void wall_accel(const WallArgs& a, int node, int y, float& gx, float& gy) {
@@ -362,6 +363,7 @@ __global__ void __launch_bounds__(kBX * kBY) wall_collide_kernel(const __grid_co
   K[0] = fmaf(-om1, m.acc, K[0]);
   apply_poly_h<L, 15>(g, K, om1, m.dr);
   using T = typename Codec<ST>::T;
+  if (!HLBM_IN(node, a.N, DBG_STORE)) return;
   T* __restrict__ fout = static_cast<T*>(a.fout) + node;
   const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(node, g[0]);
   static_for<37>([&](auto I) {

@@ -126,3 +126,11 @@ def test_allocation_failure_is_reported(abi, monkeypatch):
     assert abi.hlbm_init(ctx, r.ctypes.data, u.ctypes.data, r.ctypes.data, 0) == abi.HLBM_ENOMEM
     assert b"HLBM_FAULT_ALLOC" in abi.hlbm_last_error(ctx)
     abi.hlbm_destroy(ctx)
+
+
+def test_release_build_has_no_bounds_record(abi):
+    """hlbm_debug_record belongs to the bounds-checked build only: the release
+    library answers HLBM_EUNSUPPORTED without touching a device."""
+    out = (C.c_ulonglong * 4)()
+    assert not abi.DEBUG
+    assert abi.hlbm_debug_record(out, 1) == abi.HLBM_EUNSUPPORTED
