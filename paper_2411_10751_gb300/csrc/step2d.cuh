@@ -147,6 +147,33 @@ __device__ __forceinline__ void issue_tile(typename Cf::T* sp, const CUtensorMap
   }
 }
 
+// issue_tile with the Q boxes split over the CTA's warps: lane 0 of warp w
+// issues the planes i = w (mod W), so that no warp spends the whole issue
+// sequence while the others wait for it at the next barrier.  Every warp's
+// lane 0 calls it (the plane parameters stay compile-time constants); warp 0
+// arms the barrier (the order of arming and completion does not matter).
+template <class Cf, int W>
+__device__ __forceinline__ void issue_tile_split(typename Cf::T* sp, const CUtensorMap* tmap, uint64_t* bar, int x0,
+                                                 int y0, int skip, int nx, int ny, int warp) {
+  using L = D2Q37;
+  constexpr int H = Cf::H;
+  if (warp == 0) mbar_arrive_expect_tx(bar, Cf::TX_BYTES);
+  if (skip) return;
+  static_for<37>([&](auto I) {
+    constexpr int i = I;
+    if (i % W != warp) return;
+    const int bx = x0 - H - L::c(i, 0) - Cf::rem(i), by = y0 - H - L::c(i, 1);
+#ifdef HLBM_DEBUG
+    if (!HLBM_IN(bx % Cf::A, 1, DBG_BOX) || !HLBM_IN(bx, nx - Cf::WB + 1, DBG_BOX) ||
+        !HLBM_IN(by, ny - Cf::HB + 1, DBG_BOX))
+      return;
+#endif
+    tma_load_3d(sp + i * Cf::PLANE, tmap, bx, by, i, bar);
+  });
+  (void)nx;
+  (void)ny;
+}
+
 // Whether the tile's boxes lie inside the domain (no periodic wrap needed).
 template <class Cf>
 __device__ __forceinline__ bool tile_boxed(const StepArgs& a, int x0, int y0) {
@@ -551,41 +578,38 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
     x0 = tx * 32;
     y0 = ty * BY;
   };
-  // tid 0 takes tile indices one tile ahead, so that the counter's round
-  // trip is not on the path to the next tile's copies: at staged_done it
-  // stages the index taken during the previous tile and only then takes the
-  // next one.  It keeps the counter's raw value until that next use: reducing
-  // it at once would stall thread 0 there for the atomic's round trip, and
-  // the whole CTA behind it at the tile's last barrier.  Once it has taken an
-  // index >= T it takes no more, so a launch still takes exactly T + G values.
-  unsigned long long nxt_raw = 0;
+  // Tile indices come one tile ahead: during tile k the CTA stages tile k+1
+  // (s_ahead, published at the end of tile k-1) at staged_done, its copies
+  // split over the warps, and thread 0 takes the index of tile k+2 then; the
+  // counter's raw value is reduced only at the end of tile k, so the atomic's
+  // round trip overlaps the collision.  A CTA takes no index after its first
+  // one >= T, so a launch still takes exactly T + G values.
+  __shared__ int s_ahead;
+  unsigned long long raw = 0;
   auto take = [&]() { return atomicAdd(a.tile_ctr, 1ull); };
-  auto stage = [&](int tn) {   // tid 0: publishes tile tn and, if it is a boxed tile, stages it
-    s_next = tn;
+  auto stage = [&](int tn) {   // lane 0 of every warp: stages tile tn if it is a boxed tile
     if (tn < ntiles) {
       int xn, yn;
       origin(tn, xn, yn);
       if (aligned && tile_boxed<Cf>(a, xn, yn)) {
         fence_proxy_async_smem();
-        issue_tile<Cf>(sp, &tmap, bar, xn, yn, a.debug_skip_tma, a.nx, a.ny);
+        issue_tile_split<Cf, NT / 32>(sp, &tmap, bar, xn, yn, a.debug_skip_tma, a.nx, a.ny, tid >> 5);
       }
     }
-  };
-  auto take_and_issue = [&]() {
-    const int tn = (int)(nxt_raw % period);
-    stage(tn);
-    if (tn < ntiles) nxt_raw = take();
   };
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
-    nxt_raw = take();
-    take_and_issue();
+    const int t0 = (int)(take() % period);
+    s_next = t0;
+    s_ahead = (t0 < ntiles) ? (int)(take() % period) : t0;
   }
   __syncthreads();
+  if ((tid & 31) == 0) stage(s_next);
   uint32_t phase = 0;
   int t = s_next;
   while (t < ntiles) {
+    const int tn = s_ahead;
     int x0, y0;
     origin(t, x0, y0);
     if (aligned && tile_boxed<Cf>(a, x0, y0)) {
@@ -602,10 +626,12 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       __syncthreads();
     }
     process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, a.fout, [&] {
-      if (tid == 0) take_and_issue();
+      if ((tid & 31) == 0) stage(tn);
+      if (tid == 0 && tn < ntiles) raw = take();
     });
-    __syncthreads();  // s_next is published; the shared aux tile is reused by the next tile
-    t = s_next;
+    if (tid == 0) s_ahead = (tn < ntiles) ? (int)(raw % period) : tn;
+    __syncthreads();  // s_ahead is published; the shared aux tile is reused by the next tile
+    t = tn;
   }
 }
 
