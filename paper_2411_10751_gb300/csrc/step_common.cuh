@@ -144,7 +144,7 @@ __device__ __forceinline__ void d3_cyz(int p, int& cy, int& cz, iseq<I...>) {
 // finalizer of MurmurHash3 (Appleby).  Below the normal range (|v| < 2^-14
 // for FP16) the truncation drops more than 13 bits and rounds toward zero
 // more often; those values are a few FP16 subnormal steps from zero.
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+__host__ __device__ __forceinline__ constexpr uint32_t fmix32(uint32_t h) {
   h ^= h >> 16;
   h *= 0x85EBCA6Bu;
   h ^= h >> 13;
@@ -155,10 +155,10 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 __device__ __forceinline__ uint32_t node_salt(long long node, float g0) {
   return fmix32((uint32_t)node * 0x9E3779B1u ^ __float_as_uint(g0));
 }
-// random bits for population i of a node with salt h (a second, cheap mix)
-__device__ __forceinline__ uint32_t pop_bits(uint32_t h, int i) {
-  return (h ^ ((uint32_t)i * 0x27D4EB2Fu)) * 0x165667B1u;
-}
+// random bits for population i of a node with salt h: one multiply by an odd
+// constant of its own per population (the finalizer of i + 1, folded at
+// compile time); round_store keeps the high bits of the product
+__device__ __forceinline__ uint32_t pop_bits(uint32_t h, int i) { return h * (fmix32((uint32_t)i + 1u) | 1u); }
 template <class T> __device__ __forceinline__ T round_store(float v, uint32_t bits);
 template <> __device__ __forceinline__ float round_store<float>(float v, uint32_t) { return v; }
 template <> __device__ __forceinline__ __half round_store<__half>(float v, uint32_t bits) {
