@@ -41,25 +41,38 @@ constexpr int frame_of() {
   return KIND == KIND_SC ? 3 : (KIND == KIND_THERMAL ? 1 : 0);
 }
 
-// ODD: the step's parity; MOM: moments readout (no store).
-template <int ST, int KIND, bool ODD, bool MOM>
-__global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_constant__ StepArgs a) {
+// ODD: the step's parity; MOM: moments readout (no store).  NPT nodes per
+// thread: lane k of thread (tx, ty) is tile row ty + k kBY / NPT, and with
+// NPT = 2 the node arithmetic runs on paired FP32 lanes (float2), rounding
+// exactly like the one-node form.
+template <int ST, int KIND, bool ODD, bool MOM, int NPT>
+__global__ void __launch_bounds__(kBX * kBY / NPT, 2 * NPT) aa_step_kernel(const __grid_constant__ StepArgs a) {
   using T = typename Codec<ST>::T;
+  using V = typename std::conditional<NPT == 2, float2, float>::type;
   constexpr int H = frame_of<KIND>();
   constexpr int SW = kBX + 2 * H, SH = kBY + 2 * H;
+  constexpr int TR = kBY / NPT, NT = kBX * TR;   // thread rows, threads
   __shared__ float aux[(H > 0) ? SW * SH : 1];
-  __shared__ double red[kBY][6];
+  __shared__ double red[TR][6];
   const int nx = a.nx, ny = a.ny;
   const size_t N = (size_t)a.N;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kBX + tx;
   const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool active = x < nx && y < ny;
-  const int xc = active ? x : x % nx, yc = y < ny ? y : y % ny;   // inactive lanes still fill the frame
+  const int x = x0 + tx;
+  const int xc = x < nx ? x : x % nx;   // inactive lanes still compute (the frame is shared)
+  int yck[NPT], nodek[NPT];
+  bool activek[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    const int y = y0 + ty + k * TR;
+    activek[k] = x < nx && y < ny;
+    yck[k] = y < ny ? y : y % ny;
+    nodek[k] = yck[k] * nx + xc;
+  }
 
   // the previous step's neighbour field, on the tile and its frame
   if constexpr (H > 0) {
-    for (int k = tid; k < SW * SH; k += kBX * kBY) {
+    for (int k = tid; k < SW * SH; k += NT) {
       const int j = k / SW, i = k - j * SW;
       const int X = wrapm(x0 - H + i, nx), Y = wrapm(y0 - H + j, ny);
       aux[k] = __ldg(a.aux_rd + HLBM_IDX((long long)Y * nx + X, a.N, DBG_AUX));
@@ -67,74 +80,96 @@ __global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_cons
     __syncthreads();
   }
 
-  // the node's populations at time t
+  // the nodes' populations at time t
   const T* __restrict__ f = static_cast<const T*>(a.fin);
-  float g[37];
-  int xs[7], ys[7];
+  V g[37];
+  int xs[7], ys[NPT][7];
 #pragma unroll
   for (int d = -3; d <= 3; ++d) {
     xs[d + 3] = wrap1(xc - d, nx);
-    ys[d + 3] = wrap1(yc - d, ny) * nx;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) ys[k][d + 3] = wrap1(yck[k] - d, ny) * nx;
   }
   static_for<37>([&](auto I) {
     constexpr int i = I;
-    if constexpr (!ODD) {
-      g[i] = to_float(f[HLBM_IDX((long long)i * N + (long long)yc * nx + xc, 37 * a.N, DBG_GATHER)]);
-    } else {
-      constexpr int cx = L::c(i, 0), cy = L::c(i, 1), b = aa_opp(i);
-      g[i] = to_float(f[HLBM_IDX((long long)b * N + ys[cy + 3] + xs[cx + 3], 37 * a.N, DBG_GATHER)]);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if constexpr (!ODD) {
+        set_lane(g[i], k, to_float(f[HLBM_IDX((long long)i * N + nodek[k], 37 * a.N, DBG_GATHER)]));
+      } else {
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), b = aa_opp(i);
+        set_lane(g[i], k, to_float(f[HLBM_IDX((long long)b * N + ys[k][cy + 3] + xs[cx + 3], 37 * a.N, DBG_GATHER)]));
+      }
     }
   });
-  const int node = yc * nx + xc;
 
-  float dr, dr_l, acc, J[3], Pih;
+  V dr, dr_l, acc, J[3], Pih;
   moments_h<L>(g, dr, dr_l, acc, J, Pih);
-  const float rho = a.rho0 + dr;
-  float ga[3];
-  accel<2>(a, node, yc, ga);
-  float Fx = rho * ga[0], Fy = rho * ga[1];
-  float sigma = 0.f, psi_now = 0.f;
+  const V rho = vadd(splat<V>(a.rho0), dr);
+  V gax, gay;
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    float ga[3];
+    accel<2>(a, nodek[k], yck[k], ga);
+    set_lane(gax, k, ga[0]);
+    set_lane(gay, k, ga[1]);
+  }
+  V Fx = vmul(rho, gax), Fy = vmul(rho, gay);
+  V sigma = splat<V>(0.f), psi_now = splat<V>(0.f);
   if constexpr (KIND == KIND_SC) {
     // F^SC = -G psi(x) sum_i w_i psi(x + c_i) c_i, G = -1, psi of the previous step
-    const float* ap = aux + (ty + H) * SW + tx + H;
-    float sx = 0.f, sy = 0.f;
+    V sx = splat<V>(0.f), sy = splat<V>(0.f), ps;
     static_for<L::NPAIR>([&](auto P) {
       constexpr int i = 2 * P + 1;
       constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
-      const float dpsi = ap[cy * SW + cx] - ap[-cy * SW - cx];
-      if constexpr (cx != 0) sx = fmaf((float)(L::w(i) * cx), dpsi, sx);
-      if constexpr (cy != 0) sy = fmaf((float)(L::w(i) * cy), dpsi, sy);
+      V dpsi;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const float* ap = aux + (ty + k * TR + H) * SW + tx + H;
+        set_lane(dpsi, k, ap[cy * SW + cx] - ap[-cy * SW - cx]);
+      }
+      if constexpr (cx != 0) sx = vfma(splat<V>((float)(L::w(i) * cx)), dpsi, sx);
+      if constexpr (cy != 0) sy = vfma(splat<V>((float)(L::w(i) * cy)), dpsi, sy);
     });
-    const float ps = ap[0];
-    const float fsx = ps * sx, fsy = ps * sy;
-    Fx += fsx;
-    Fy += fsy;
-    sigma = (ps > 0.f) ? a.p_coef * (fsx * fsx + fsy * fsy) * rcp_nr(ps * ps) : 0.f;
-    psi_now = psi_of<L>(a, dr, dr_l);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) set_lane(ps, k, aux[(ty + k * TR + H) * SW + tx + H]);
+    const V fsx = vmul(ps, sx), fsy = vmul(ps, sy);
+    Fx = vadd(Fx, fsx);
+    Fy = vadd(Fy, fsy);
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      const float p1 = lane(ps, k), f1 = lane(fsx, k), f2 = lane(fsy, k);
+      set_lane(sigma, k, (p1 > 0.f) ? a.p_coef * (f1 * f1 + f2 * f2) * rcp_nr(p1 * p1) : 0.f);
+      set_lane(psi_now, k, psi_of<L>(a, lane(dr, k), lane(dr_l, k)));
+    }
   }
   constexpr float Dc = (float)(2.0 * L::cs2);
-  const float inv_rho = rcp_nr(rho);
-  const float ux = fmaf(0.5f, Fx, J[0]) * inv_rho;
-  const float uy = fmaf(0.5f, Fy, J[1]) * inv_rho;
-  const float uu = fmaf(ux, ux, uy * uy);
-  const float G2 = fmaf(Dc, sigma, 2.f * fmaf(ux, Fx, uy * Fy));
-  const float tb = (fmaf(0.5f, G2, Pih - rho * uu) * inv_rho) * (1.f / Dc);
+  const V inv_rho = vmap(rho, [](float r) { return rcp_nr(r); });
+  const V ux = vmul(vfma(splat<V>(0.5f), Fx, J[0]), inv_rho);
+  const V uy = vmul(vfma(splat<V>(0.5f), Fy, J[1]), inv_rho);
+  const V uu = vfma(ux, ux, vmul(uy, uy));
+  const V G2 = vfma(splat<V>(Dc), sigma, vmul(splat<V>(2.f), vfma(ux, Fx, vmul(uy, Fy))));
+  const V tb = vmul(vmul(vfma(splat<V>(0.5f), G2, vsub(Pih, vmul(rho, uu))), inv_rho), splat<V>(1.f / Dc));
 
   if constexpr (MOM) {
     double v[6] = {0, 0, 0, 0, 0, 0};
-    if (active) {
-      if (a.rho_out) a.rho_out[node] = rho;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if (!activek[k]) continue;
+      const int node = nodek[k];
+      const float r = lane(rho, k), vx = lane(ux, k), vy = lane(uy, k), t = lane(tb, k);
+      if (a.rho_out) a.rho_out[node] = r;
       if (a.u_out) {
-        a.u_out[node] = ux;
-        a.u_out[N + node] = uy;
+        a.u_out[node] = vx;
+        a.u_out[N + node] = vy;
       }
-      if (a.theta_out) a.theta_out[node] = 1.f + tb;
-      const bool bad = !(isfinite(rho) && rho > 0.f && isfinite(ux) && isfinite(uy) && isfinite(tb));
-      v[0] = dr;
-      v[1] = (double)rho * ux;
-      v[2] = (double)rho * uy;
-      v[4] = 0.5 * ((double)Pih + (double)Dc * dr + 0.5 * (double)G2);
-      v[5] = bad ? 1.0 : 0.0;
+      if (a.theta_out) a.theta_out[node] = 1.f + t;
+      const bool bad = !(isfinite(r) && r > 0.f && isfinite(vx) && isfinite(vy) && isfinite(t));
+      v[0] += lane(dr, k);
+      v[1] += (double)r * vx;
+      v[2] += (double)r * vy;
+      v[4] += 0.5 * ((double)lane(Pih, k) + (double)Dc * lane(dr, k) + 0.5 * (double)lane(G2, k));
+      v[5] += bad ? 1.0 : 0.0;
     }
     if (a.partials) {
 #pragma unroll
@@ -146,59 +181,84 @@ __global__ void __launch_bounds__(kBX * kBY, 2) aa_step_kernel(const __grid_cons
       __syncthreads();
       if (tid < 6) {
         double sum = 0.0;
-        for (int w = 0; w < kBY; ++w) sum += red[w][tid];
+        for (int w = 0; w < TR; ++w) sum += red[w][tid];
         a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + tid] = sum;
       }
     }
     return;
   } else {
-    if (!active || !HLBM_IN(node, a.N, DBG_STORE)) return;
     // this step's field for the next step's neighbours
-    if constexpr (KIND == KIND_SC) a.aux_wr[node] = psi_now;
-    if constexpr (KIND == KIND_THERMAL) a.aux_wr[node] = tb;
-    NodeSrcT<float> s;
-    s.hG[0] = s.hG[1] = s.hG[2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if (!activek[k]) continue;
+      if constexpr (KIND == KIND_SC) a.aux_wr[nodek[k]] = lane(psi_now, k);
+      if constexpr (KIND == KIND_THERMAL) a.aux_wr[nodek[k]] = lane(tb, k);
+    }
+    NodeSrcT<V> s;
+    s.hG[0] = s.hG[1] = s.hG[2] = splat<V>(0.f);
     if constexpr (KIND == KIND_THERMAL) {
-      const float* ap = aux + (ty + 1) * SW + tx + 1;
-      const float gtx = 0.5f * (ap[1] - ap[-1]);
-      const float gty = 0.5f * (ap[SW] - ap[-SW]);
+      V gtx, gty;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const float* ap = aux + (ty + k * TR + 1) * SW + tx + 1;
+        set_lane(gtx, k, 0.5f * (ap[1] - ap[-1]));
+        set_lane(gty, k, 0.5f * (ap[SW] - ap[-SW]));
+      }
       // s^(3) += rho theta (1 - 1/Pr) [delta grad_xi theta], grad_xi = c0 grad
-      const float hc = rho * (1.f + tb) * (a.h_coef * (float)L::c0);
-      s.hG[0] = hc * gtx;
-      s.hG[1] = hc * gty;
+      const V hc = vmul(vmul(rho, vadd(splat<V>(1.f), tb)), splat<V>(a.h_coef * (float)L::c0));
+      s.hG[0] = vmul(hc, gtx);
+      s.hG[1] = vmul(hc, gty);
     }
     constexpr float inv_c0 = (float)(1.0 / L::c0);
-    s.dr = 0.f;
+    s.dr = splat<V>(0.f);
     s.rho = rho;
-    s.tb = a.isothermal ? 0.f : tb;
-    s.u[0] = ux * inv_c0;
-    s.u[1] = uy * inv_c0;
-    s.u[2] = 0.f;
-    s.F[0] = Fx * inv_c0;
-    s.F[1] = Fy * inv_c0;
-    s.F[2] = 0.f;
+    s.tb = a.isothermal ? splat<V>(0.f) : tb;
+    s.u[0] = vmul(ux, splat<V>(inv_c0));
+    s.u[1] = vmul(uy, splat<V>(inv_c0));
+    s.u[2] = splat<V>(0.f);
+    s.F[0] = vmul(Fx, splat<V>(inv_c0));
+    s.F[1] = vmul(Fy, splat<V>(inv_c0));
+    s.F[2] = splat<V>(0.f);
     s.sigma = sigma;
-    float K[15];
+    V K[15];
     poly2<L>(s, a.omega, a.beta, K);
     const float om1 = 1.f - a.omega;
-    K[0] = fmaf(-om1, acc, K[0]);
-    if constexpr (KIND == KIND_SC) K[0] += dr_l;
+    K[0] = vfma(splat<V>(-om1), acc, K[0]);
+    if constexpr (KIND == KIND_SC) K[0] = vadd(K[0], dr_l);
     apply_poly_h<L, 15>(g, K, om1, dr);
-    // 16-bit storage: stochastic rounding keyed by node and result (step_common.cuh)
-    const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(node, g[0]);
     T* __restrict__ fo = static_cast<T*>(a.fout);
-    static_for<37>([&](auto I) {
-      constexpr int i = I;
-      constexpr int b = aa_opp(i);
-      const T v = round_store<T>(g[i], pop_bits(salt, i));
-      if constexpr (!ODD) {
-        fo[(size_t)b * N + node] = v;                             // slot ibar of x
-      } else {
-        constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
-        const long long o = (long long)i * N + ys[3 - cy] + xs[3 - cx];
-        if (HLBM_IN(o, 37 * a.N, DBG_STORE)) fo[o] = v;           // slot i of x + c_i
-      }
-    });
+    // the odd step's store offsets are recomputed here from a copy of x that
+    // the compiler cannot match with the load offsets, so that the loads'
+    // offset arrays need not stay live across the collision
+    int xl = xc;
+    asm volatile("" : "+r"(xl));
+    int xt[7];
+#pragma unroll
+    for (int d = -3; d <= 3; ++d) xt[d + 3] = ODD ? wrap1(xl + d, nx) : 0;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if (!activek[k] || !HLBM_IN(nodek[k], a.N, DBG_STORE)) continue;
+      const int node = nodek[k];
+      int yl = yck[k];
+      asm volatile("" : "+r"(yl));
+      int yt[7];
+#pragma unroll
+      for (int d = -3; d <= 3; ++d) yt[d + 3] = ODD ? wrap1(yl + d, ny) * nx : 0;
+      // 16-bit storage: stochastic rounding keyed by node and result (step_common.cuh)
+      const uint32_t salt = std::is_same<T, float>::value ? 0u : node_salt(node, lane(g[0], k));
+      static_for<37>([&](auto I) {
+        constexpr int i = I;
+        constexpr int b = aa_opp(i);
+        const T v = round_store<T>(lane(g[i], k), pop_bits(salt, i));
+        if constexpr (!ODD) {
+          fo[(size_t)b * N + node] = v;                             // slot ibar of x
+        } else {
+          constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
+          const long long o = (long long)i * N + yt[cy + 3] + xt[cx + 3];
+          if (HLBM_IN(o, 37 * a.N, DBG_STORE)) fo[o] = v;           // slot i of x + c_i
+        }
+      });
+    }
   }
 }
 
@@ -236,15 +296,18 @@ __global__ void __launch_bounds__(256) aa_init_kernel(const __grid_constant__ St
   if constexpr (KIND == KIND_SC) a.aux_wr[n] = psi_of<L>(a, rho[n] - a.rho0, 0.f);
 }
 
+// steps: two nodes per thread (paired FP32 lanes); the moments readout: one
 template <int ST, int KIND>
 cudaError_t launch_kind(const StepArgs& a, bool odd, bool mom, cudaStream_t s) {
-  const dim3 block(kBX, kBY), grid((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY);
+  const dim3 grid((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY);
   if (mom) {
-    if (odd) aa_step_kernel<ST, KIND, true, true><<<grid, block, 0, s>>>(a);
-    else aa_step_kernel<ST, KIND, false, true><<<grid, block, 0, s>>>(a);
+    const dim3 block(kBX, kBY);
+    if (odd) aa_step_kernel<ST, KIND, true, true, 1><<<grid, block, 0, s>>>(a);
+    else aa_step_kernel<ST, KIND, false, true, 1><<<grid, block, 0, s>>>(a);
   } else {
-    if (odd) aa_step_kernel<ST, KIND, true, false><<<grid, block, 0, s>>>(a);
-    else aa_step_kernel<ST, KIND, false, false><<<grid, block, 0, s>>>(a);
+    const dim3 block(kBX, kBY / 2);
+    if (odd) aa_step_kernel<ST, KIND, true, false, 2><<<grid, block, 0, s>>>(a);
+    else aa_step_kernel<ST, KIND, false, false, 2><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
