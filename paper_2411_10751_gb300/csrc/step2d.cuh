@@ -47,6 +47,7 @@ struct Cfg2 {
   static constexpr int AUX_BYTES = (H > 0) ? ((RW * RH * 4 + 127) / 128) * 128 : 0;
   static constexpr int RED_BYTES = MOM ? ((NT / 32) * 6 * 8 + 127) / 128 * 128 : 0;
   static constexpr int SMEM = POP_BYTES + AUX_BYTES + RED_BYTES + 128;  // + mbarrier
+  static constexpr int OUT_BYTES = L::Q * BX * BY * (int)sizeof(T);        // separately staged results
   static constexpr uint32_t TX_BYTES = (uint32_t)L::Q * WB * HB * (uint32_t)sizeof(T);
   __host__ __device__ static constexpr int rem(int i) { return ((-H - L::c(i, 0)) % A + A) % A; }
 };
@@ -210,7 +211,11 @@ __device__ __forceinline__ void fill_tile_wrapped(const StepArgs& a, const void*
 // staging buffer has finished (after a CTA barrier), so a caller may start
 // refilling it then.  TMA_STORE: results leave through the staging buffer by
 // bulk tensor stores.
-template <int ST, int KIND, bool MOM, int BY, int NPT, bool TMA_STORE, class Done>
+// SEP_OUT: the results are staged for their bulk stores in a buffer of
+// their own behind the tile's shared memory (Cfg2::OUT_BYTES at Cfg2::SMEM;
+// planes of 32 x BY), so that the next tile may already be landing in the
+// input planes.
+template <int ST, int KIND, bool MOM, int BY, int NPT, bool TMA_STORE, bool SEP_OUT = false, class Done>
 __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMap* tmap_out, unsigned char* smem,
                                              int x0, int y0, void* fout_v, Done&& staged_done) {
   using Cf = Cfg2<ST, KIND, MOM, BY>;
@@ -411,19 +416,22 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, const CUtensorMa
       // stage the tile's results densely in the (now unused) input planes and
       // write each plane with one bulk tensor store; out-of-domain rows and
       // columns of a ragged tile are clipped by the copy
+      constexpr int OP = SEP_OUT ? BX * BY : Cf::PLANE;   // plane stride of the staged results
+      T* const so = SEP_OUT ? reinterpret_cast<T*>(smem + Cf::SMEM) : sp;
       __syncthreads();
       static_for<37>([&](auto I) {
         constexpr int i = I;
 #pragma unroll
         for (int k = 0; k < NPT; ++k)
-          sp[stg<Cf>(i, (ty + k * TR) * BX + tx)] = round_store<T>(lane(g[i], k), pop_bits(salt[k], i));
+          so[i * OP + HLBM_IDX((ty + k * TR) * BX + tx, BX * BY, DBG_STAGE)] =
+              round_store<T>(lane(g[i], k), pop_bits(salt[k], i));
       });
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
         static_for<37>([&](auto I) {
           constexpr int i = I;
-          tma_store_3d(tmap_out, sp + i * Cf::PLANE, x0, y0, i);
+          tma_store_3d(tmap_out, so + i * OP, x0, y0, i);
         });
         bulk_commit();
         bulk_wait_read_all();   // the staging buffer has been read; the writes complete with the grid
@@ -538,9 +546,30 @@ struct TileSplit {
 // differ.  The counter is never reset between launches: a launch of G CTAs
 // over T tiles takes exactly T + G values (every CTA stops at its first index
 // >= T), so the tile is the counter value mod (T + G).
+// 16-bit storage: results leave by bulk tensor stores from a staging buffer
+// of their own (the input planes hold the next tile by then); FP32 storage,
+// whose 63 KB of staging leaves no room for it: coalesced global stores.
+template <int ST>
+constexpr bool persistent_sep_out() {
+  return ST != ST_F32;
+}
+template <int ST, int KIND, int BY>
+constexpr int persistent_smem() {
+  return Cfg2<ST, KIND, false, BY>::SMEM + (persistent_sep_out<ST>() ? Cfg2<ST, KIND, false, BY>::OUT_BYTES : 0);
+}
+
 template <int ST, int KIND, int BY, int NPT>
-__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY, NPT>()))
-    step2d_persistent_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap) {
+constexpr int min_ctas_persistent() {
+  constexpr int threads = 32 * BY / NPT;
+  constexpr int by_smem = (227 * 1024) / persistent_smem<ST, KIND, BY>();
+  constexpr int cap = (threads >= 512) ? 2 : (threads <= 128 ? 4 : 3);
+  return by_smem < 1 ? 1 : (by_smem < cap ? by_smem : cap);
+}
+
+template <int ST, int KIND, int BY, int NPT>
+__global__ void __launch_bounds__(32 * BY / NPT, (min_ctas_persistent<ST, KIND, BY, NPT>()))
+    step2d_persistent_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap,
+                             const __grid_constant__ CUtensorMap tmap_out) {
   using Cf = Cfg2<ST, KIND, false, BY>;
   constexpr int NT = 32 * BY / NPT;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -625,7 +654,8 @@ __global__ void __launch_bounds__(32 * BY / NPT, (min_ctas2<ST, KIND, false, BY,
       fill_tile_wrapped<Cf, NT>(a, a.fin, sp, x0, y0, tid);
       __syncthreads();
     }
-    process_tile<ST, KIND, false, BY, NPT, false>(a, nullptr, smem, x0, y0, a.fout, [&] {
+    constexpr bool SEP = persistent_sep_out<ST>();
+    process_tile<ST, KIND, false, BY, NPT, SEP, SEP>(a, &tmap_out, smem, x0, y0, a.fout, [&] {
       if ((tid & 31) == 0) stage(tn);
       if (tid == 0 && tn < ntiles) raw = take();
     });
@@ -816,7 +846,7 @@ cudaError_t configure2() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg2<ST, KIND, MOM, BY>::SMEM);
   if (e != cudaSuccess || MOM) return e;
   e = cudaFuncSetAttribute(step2d_persistent_kernel<ST, KIND, BY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           Cfg2<ST, KIND, false, BY>::SMEM);
+                           persistent_smem<ST, KIND, BY>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(step2d_multistep_kernel<ST, KIND, BY, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Cfg2<ST, KIND, false, BY>::SMEM);
@@ -830,7 +860,7 @@ int persistent_ctas() {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step2d_persistent_kernel<ST, KIND, BY, NPT>, 32 * BY / NPT,
-                                                  Cfg2<ST, KIND, false, BY>::SMEM);
+                                                  persistent_smem<ST, KIND, BY>());
     return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   });
 }
@@ -866,9 +896,13 @@ cudaError_t launch2(const StepArgs& a, const CUtensorMap* tmaps, cudaStream_t s)
     if (a.persistent) {
       const int tiles = ((a.nx + 31) / 32) * ((a.ny + BY - 1) / BY);
       const int ctas = std::min(tiles, persistent_ctas<ST, KIND, BY, NPT>());
-      CUtensorMap tm{};
-      if (tmaps) tm = tmaps[0];
-      step2d_persistent_kernel<ST, KIND, BY, NPT><<<ctas, dim3(32, BY / NPT, 1), Cf::SMEM, s>>>(a, tm);
+      CUtensorMap tm{}, tmo{};
+      if (tmaps) {
+        tm = tmaps[0];
+        tmo = tmaps[1];
+      }
+      step2d_persistent_kernel<ST, KIND, BY, NPT>
+          <<<ctas, dim3(32, BY / NPT, 1), persistent_smem<ST, KIND, BY>(), s>>>(a, tm, tmo);
       return cudaGetLastError();
     }
   }
