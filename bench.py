@@ -55,6 +55,12 @@ WORKLOADS = {
     "tg3d256": (lambda: W.taylor_green_3d(n=256), "D3Q39 compressible Taylor-Green 256^3, Ma=0.3, tau=0.6, body force"),
     "droplet512": (lambda: W.droplet(n=512), "D2Q37 vdW droplet 512x512 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8"),
     "droplet1024": (lambda: W.droplet(n=1024), "D2Q37 vdW droplet 1024x1024 (T/Tc 0.85, k 0.01, r0 N/4), tau=0.8"),
+    # wall-bounded step (Tamm-Mott-Smith walls, two launches per step) and the
+    # Carnahan-Starling pseudopotential
+    "rb1024": (lambda: W.rayleigh_benard(nx=1024, ny=1026, Ra=10000.0, roll=0.01),
+               "D2Q37 Rayleigh-Benard, 1024x1026 between two walls (Ra 1e4, Pr 1.41, theta 1.4 / 1.0)"),
+    "csdroplet1024": (lambda: W.droplet(n=1024, r0=256.0, Tr=0.8, k=3.02, eos="cs"),
+                      "D2Q37 Carnahan-Starling droplet 1024x1024 (T/Tc 0.8, k 3.02, r0 N/4), tau=0.8"),
     # the in-place (AA) step with single-pass neighbour fields
     "thermal1024_aa": (lambda: _lagged(W.thermal_decay(n=1024)), WORKLOAD + ", in place (AA), single-pass"),
     "droplet1024_aa": (lambda: _lagged(W.droplet(n=1024)),
@@ -127,6 +133,8 @@ def _multistep(case, sched) -> bool:
 def _launches(case, sched, steps) -> int:
     """Step-kernel launches of hlbm_step(steps): one per step, or one per
     block of up to 1024 steps for the multi-step kernel."""
+    if case.params.get("walls"):
+        return 2 * steps   # completion + moments, then collision
     if not _multistep(case, sched):
         return steps
     tiles = (case.nx // 32) * (case.ny // sched[0])
@@ -738,7 +746,9 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _ncu_traffic(khash, args.storage, sched, args.workload),
                          "algorithmic_bytes_per_node": bytes_per_node,
-                         "kernel": "aa_step_kernel (in place, one launch per step)" if case.params.get("lag") else
+                         "kernel": "wall_moments_kernel + wall_collide_kernel (two launches per step, the "
+                                   "populations read in both)" if case.params.get("walls") else
+                                   "aa_step_kernel (in place, one launch per step)" if case.params.get("lag") else
                                    (("step3d_rows_kernel" if sched[2] >= 2 and case.nx in (32, 64, 128, 256)
                                      else "step3d_kernel") if case.lattice == "D3Q39" else
                                     ("step2d_multistep_kernel" if _multistep(case, sched) else
