@@ -72,12 +72,28 @@ __device__ __forceinline__ void gauss_moments_d(double u, double tb, double (&m)
   m[3] = u * (u2 + 3.0 * tb);
   m[4] = u2 * (u2 + 6.0 * tb) + 3.0 * tb * tb;
 }
-template <int I>
-__device__ __forceinline__ double peq_m1(double ux, double uy, double tb) {
-  constexpr int cx = L::c(I, 0), cy = L::c(I, 1);
+// P_i - 1 from precomputed products: hp[k] = m_a(u_x) m_b(u_y) for
+// the 14 index pairs (a, b) with 1 <= a + b <= 4 (k = hk(a, b)), so that the
+// completion forms the products once per state (the node's previous moments,
+// and one wall target per |c_y|) and then costs 14 FP64 multiply-adds per
+// population instead of a whole expansion.
+__host__ __device__ constexpr int hk(int a, int b) {
+  return (a + b == 1) ? a : (a + b == 2) ? 2 + a : (a + b == 3) ? 5 + a : 9 + a;
+}
+__device__ __forceinline__ void herm_prod(double ux, double uy, double tb, double (&hp)[14]) {
   double mx[5], my[5];
   gauss_moments_d(ux * (1.0 / L::c0), tb, mx);
   gauss_moments_d(uy * (1.0 / L::c0), tb, my);
+  static_for<5>([&](auto A) {
+    static_for<5>([&](auto B) {
+      constexpr int a = A, b = B;
+      if constexpr (a + b >= 1 && a + b <= L::FEQ_ORDER) hp[hk(a, b)] = mx[a] * my[b];
+    });
+  });
+}
+template <int I>
+__device__ __forceinline__ double peq_m1_hp(const double (&hp)[14]) {
+  constexpr int cx = L::c(I, 0), cy = L::c(I, 1);
   double acc = 0.0;
   static_for<5>([&](auto A) {
     static_for<5>([&](auto B) {
@@ -94,7 +110,7 @@ __device__ __forceinline__ double peq_m1(double ux, double uy, double tb) {
           return s;
         }();
         constexpr double cf = hx * hy / (fact_d(a) * fact_d(b));
-        if constexpr (cf != 0.0) acc = fma(cf, mx[a] * my[b], acc);
+        if constexpr (cf != 0.0) acc = fma(cf, hp[hk(a, b)], acc);
       }
     });
   });
@@ -145,20 +161,28 @@ __device__ __forceinline__ void wall_gather(const WallArgs& a, int x, int y, flo
   const double u1x = __ldg(a.mprev + N + node1), u1y = __ldg(a.mprev + 2 * N + node1);
   const double tb1 = __ldg(a.mprev + 3 * N + node1);
   const double uwx = a.wall_u[side][0], uwy = a.wall_u[side][1], tbw = a.wall_tb[side];
+  // Hermite products of the previous moments and of the wall target of each
+  // |c_y| = 1, 2, 3 (extrapolated to the turning point)
+  double hpp[14], hpt[3][14];
+  herm_prod(upx, upy, tbp, hpp);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double wgt = (double)(2 + k - 2 * r);   // (1/2 - turning point) / (1/2), |c_y| = k + 1
+    herm_prod(fma(wgt, uwx - u1x, uwx), fma(wgt, uwy - u1y, uwy), fma(wgt, tbw - tb1, tbw), hpt[k]);
+  }
   // sums over the unknowns of w P_i(targets) - w and w P_ibar(p) - w
   double W = 0.0, A = 0.0, B = 0.0;
   static_for<37>([&](auto I) {
     constexpr int i = I;
     constexpr int cy = L::c(i, 1), ab = cy < 0 ? -cy : cy;
     constexpr int b = opp_of(i);
-    if (y - cy < 0 || y - cy >= ny) {
-      const double wgt = (double)(1 + ab - 2 * r);   // (1/2 - turning point) / (1/2)
-      const double ux = fma(wgt, uwx - u1x, uwx), uy = fma(wgt, uwy - u1y, uwy);
-      const double tb = fma(wgt, tbw - tb1, tbw);
-      constexpr double w = L::w(i);
-      W += w;
-      A = fma(w, peq_m1<i>(ux, uy, tb), A);
-      B = fma(w, peq_m1<b>(upx, upy, tbp), B);
+    if constexpr (ab > 0) {
+      if (y - cy < 0 || y - cy >= ny) {
+        constexpr double w = L::w(i);
+        W += w;
+        A = fma(w, peq_m1_hp<i>(hpt[ab - 1]), A);
+        B = fma(w, peq_m1_hp<b>(hpp), B);
+      }
     }
   });
   const double sm1 = (B - A) / (W + A);            // s - 1
@@ -166,13 +190,12 @@ __device__ __forceinline__ void wall_gather(const WallArgs& a, int x, int y, flo
     constexpr int i = I;
     constexpr int cy = L::c(i, 1), ab = cy < 0 ? -cy : cy;
     constexpr int b = opp_of(i);
-    if (y - cy < 0 || y - cy >= ny) {
-      const double wgt = (double)(1 + ab - 2 * r);
-      const double ux = fma(wgt, uwx - u1x, uwx), uy = fma(wgt, uwy - u1y, uwy);
-      const double tb = fma(wgt, tbw - tb1, tbw);
-      const double pi = peq_m1<i>(ux, uy, tb), pb = peq_m1<b>(upx, upy, tbp);
-      // s P_i - P_ibar = (s - 1) + s (P_i - 1) - (P_ibar - 1)
-      g[i] = (float)fma(rp, sm1 + fma(sm1, pi, pi) - pb, (double)ldpop<ST>(a, b, x, y));
+    if constexpr (ab > 0) {
+      if (y - cy < 0 || y - cy >= ny) {
+        const double pi = peq_m1_hp<i>(hpt[ab - 1]), pb = peq_m1_hp<b>(hpp);
+        // s P_i - P_ibar = (s - 1) + s (P_i - 1) - (P_ibar - 1)
+        g[i] = (float)fma(rp, sm1 + fma(sm1, pi, pi) - pb, (double)ldpop<ST>(a, b, x, y));
+      }
     }
   });
 }
