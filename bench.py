@@ -134,7 +134,7 @@ def _launches(case, sched, steps) -> int:
     """Step-kernel launches of hlbm_step(steps): one per step, or one per
     block of up to 1024 steps for the multi-step kernel."""
     if case.params.get("walls"):
-        return 2 * steps   # completion + moments, then collision
+        return 3 * steps   # wall completion, moments, collision
     if not _multistep(case, sched):
         return steps
     tiles = (case.nx // 32) * (case.ny // sched[0])
@@ -746,7 +746,7 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _ncu_traffic(khash, args.storage, sched, args.workload),
                          "algorithmic_bytes_per_node": bytes_per_node,
-                         "kernel": "wall_moments_kernel + wall_collide_kernel (two launches per step, the "
+                         "kernel": "wall_complete_kernel + wall_moments_kernel + wall_collide_kernel (three launches per step, the "
                                    "populations read in both)" if case.params.get("walls") else
                                    "aa_step_kernel (in place, one launch per step)" if case.params.get("lag") else
                                    (("step3d_rows_kernel" if sched[2] >= 2 and case.nx in (32, 64, 128, 256)

@@ -59,6 +59,7 @@ struct hlbm_ctx {
   // fields: aux[cur ^ 1] is read by the next step, aux[cur] written
   bool aa = false;
   float* aux[2] = {nullptr, nullptr};
+  float* comp = nullptr;          // walls: completed unknowns of the six wall rows
 
   bool failed = false;
   std::string msg;
@@ -96,7 +97,7 @@ namespace {
 
 struct Layout {
   size_t pop_bytes, off_pop1, off_g, off_part, off_red, off_flags, nflags, off_mom, mom_bytes, off_aux, aux_bytes,
-      total;
+      off_comp, comp_bytes, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -122,7 +123,10 @@ Layout layout(int lattice, int nx, int ny, int nz, const hlbm_source_params* p) 
   L.mom_bytes = (p->flags & HLBM_WALLS) ? align256((size_t)4 * (size_t)N * 4) : 0;
   L.off_aux = L.off_mom + 2 * L.mom_bytes;
   L.aux_bytes = (p->flags & HLBM_AA) ? align256((size_t)N * 4) : 0;
-  L.total = L.off_aux + 2 * L.aux_bytes;
+  // walls: the completed unknowns of the six wall rows, [6][37][nx] FP32
+  L.off_comp = L.off_aux + 2 * L.aux_bytes;
+  L.comp_bytes = (p->flags & HLBM_WALLS) ? align256((size_t)6 * 37 * (size_t)nx * 4) : 0;
+  L.total = L.off_comp + L.comp_bytes;
   return L;
 }
 
@@ -241,6 +245,7 @@ void carve(hlbm_ctx* c) {
   c->mom[1] = L.mom_bytes ? reinterpret_cast<float*>(c->arena + L.off_mom + L.mom_bytes) : nullptr;
   c->aux[0] = L.aux_bytes ? reinterpret_cast<float*>(c->arena + L.off_aux) : nullptr;
   c->aux[1] = L.aux_bytes ? reinterpret_cast<float*>(c->arena + L.off_aux + L.aux_bytes) : nullptr;
+  c->comp = L.comp_bytes ? reinterpret_cast<float*>(c->arena + L.off_comp) : nullptr;
 }
 
 hlbm_status ensure_stream(hlbm_ctx* c) {
@@ -419,6 +424,7 @@ WallArgs make_wall_args(const hlbm_ctx* c) {
   w.e_ref = (float)(c->p.rho0 * 2.0 * D2Q37::cs2 * tbr);
   w.mprev = c->mom[c->cur];
   w.fin = c->pop[c->cur];
+  w.comp = c->comp;
   return w;
 }
 
@@ -427,10 +433,12 @@ WallArgs make_wall_args(const hlbm_ctx* c) {
 cudaError_t wall_step(hlbm_ctx* c) {
   WallArgs w = make_wall_args(c);
   w.mcur = c->mom[c->cur ^ 1];
-  cudaError_t e = launch_walls(w, c->storage, false, false, c->stream);
+  cudaError_t e = launch_walls(w, c->storage, 2, false, c->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_walls(w, c->storage, 0, false, c->stream);
   if (e != cudaSuccess) return e;
   w.fout = c->pop[c->cur ^ 1];
-  e = launch_walls(w, c->storage, true, c->kind == KIND_THERMAL, c->stream);
+  e = launch_walls(w, c->storage, 1, c->kind == KIND_THERMAL, c->stream);
   c->cur ^= 1;
   return e;
 }
@@ -780,7 +788,8 @@ hlbm_status hlbm_moments(hlbm_ctx* c, float* rho, float* u, float* theta, int on
     w.rho_out = a.rho_out;
     w.u_out = a.u_out;
     w.theta_out = a.theta_out;
-    e = launch_walls(w, c->storage, false, false, c->stream);
+    e = launch_walls(w, c->storage, 2, false, c->stream);
+    if (e == cudaSuccess) e = launch_walls(w, c->storage, 0, false, c->stream);
   } else if (c->aa) {
     e = aa_step(c, true, &a);
   } else {
@@ -810,7 +819,8 @@ hlbm_status hlbm_diag(hlbm_ctx* c, double* out) {
   if (c->walls) {
     WallArgs w = make_wall_args(c);
     w.partials = c->partials;
-    HLBM_CUDA(c, launch_walls(w, c->storage, false, false, c->stream), "moments kernel");
+    HLBM_CUDA(c, launch_walls(w, c->storage, 2, false, c->stream), "wall completion kernel");
+    HLBM_CUDA(c, launch_walls(w, c->storage, 0, false, c->stream), "moments kernel");
   } else if (c->aa) {
     HLBM_CUDA(c, aa_step(c, true, &a), "moments kernel");
   } else {

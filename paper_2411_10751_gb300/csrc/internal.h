@@ -117,6 +117,7 @@ struct WallArgs {
   float wall_tb[2];       // their temperature minus 1
   float tb_ref;           // reference temperature of the stored deviations minus 1
   float e_ref;            // rho0 D c0^2 tb_ref: energy moment of the reference offset
+  float* comp;            // completed unknowns of the six wall rows, [6][37][nx] (slot 3 side + r)
 };
 
 // Arguments of the initialisation kernel.
@@ -160,10 +161,11 @@ cudaError_t launch_aa(const StepArgs& a, int kind, int storage, bool odd, bool m
 cudaError_t launch_aa_init(const StepArgs& a, int kind, int storage, const float* rho, const float* u,
                            const float* theta, cudaStream_t s);
 
-// Wall-bounded D2Q37 step (walls.cu): collide false = the moments launch
-// (completion, moments into mcur / the readout pointers, partials), true =
-// the collide launch (thermal: with H_i).
-cudaError_t launch_walls(const WallArgs& a, int storage, bool collide, bool thermal, cudaStream_t s);
+// Wall-bounded D2Q37 step (walls.cu), in launch order: mode 2 = the FP64
+// completion of the wall rows' unknowns into a.comp, mode 0 = the moments
+// launch (moments into mcur / the readout pointers, partials), mode 1 = the
+// collide launch (thermal: with H_i).  Modes 0 and 1 read a.comp.
+cudaError_t launch_walls(const WallArgs& a, int storage, int mode, bool thermal, cudaStream_t s);
 // Initial state of a wall-bounded context into a.fout and m [4][N] = rho,
 // u_x, u_y, theta - 1 of the initial fields.
 cudaError_t launch_wall_init(const WallArgs& a, int storage, const float* rho, const float* u, const float* theta,

@@ -32,14 +32,15 @@
 // (h* = (1 - omega) h + omega (g^eq - r) + beta S), and the completion is
 // the same in h as in g (r_i = r_ibar).
 //
-// Each step is two launches: wall_moments_kernel completes every node and
-// writes its moments (rho, u, theta - 1) of time t, which are the next step's
-// targets and the neighbour temperatures of grad theta; wall_collide_kernel
-// completes again (same arithmetic), collides (Eq. 4.4 with F_i and H_i) and
-// stores.  grad theta is a second-order central difference, one-sided into
-// the fluid at the wall rows.  Two reads of the populations per step: these
-// domains are the paper's validation cases, a few thousand to a few hundred
-// thousand nodes.
+// Each step is three launches: wall_complete_kernel completes the unknowns of
+// the six wall rows in FP64 into a small buffer; wall_moments_kernel pulls
+// every node's populations (the unknowns from that buffer) and writes its
+// moments (rho, u, theta - 1) of time t, which are the next step's targets and
+// the neighbour temperatures of grad theta; wall_collide_kernel pulls again,
+// collides (Eq. 4.4 with F_i and H_i) and stores.  grad theta is a
+// second-order central difference, one-sided into the fluid at the wall rows.
+// Two reads of the populations per step: these domains are the paper's
+// validation cases, a few thousand to a few hundred thousand nodes.
 #include "internal.h"
 #include "lattice.cuh"
 #include "step_common.cuh"
@@ -138,20 +139,17 @@ __device__ __forceinline__ void wall_accel(const WallArgs& a, int node, int y, f
   }
 }
 
-// The 37 populations of node (x, y) at time t after streaming, the unknowns
-// completed at the walls.
+// Completion of the unknowns of a wall-row node (x, y), r = 0, 1, 2 rows from
+// its wall node: written to a.comp[slot][i][x] (slot = 3 side + r) for every
+// unknown i.  It runs once per step, before the two launches that read the
+// populations, in a launch of its own over the six wall rows, so that its
+// FP64 arithmetic neither stalls the blocks of the full-domain launches nor
+// is done twice.
 template <int ST>
-__device__ __forceinline__ void wall_gather(const WallArgs& a, int x, int y, float (&g)[37]) {
+__device__ __forceinline__ void wall_complete(const WallArgs& a, int x, int y) {
   const int nx = a.nx, ny = a.ny;
-  static_for<37>([&](auto I) {
-    constexpr int i = I;
-    constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
-    const int ys = y - cy;
-    g[i] = (ys >= 0 && ys < ny) ? ldpop<ST>(a, i, wrapx(x - cx, nx), ys) : 0.f;
-  });
   const int side = (y < ny / 2) ? 0 : 1;
   const int r = side == 0 ? y : ny - 1 - y;
-  if (r >= 3) return;
   const size_t N = (size_t)a.N;
   const int node = y * nx + x;
   const int node1 = (side == 0 ? 1 : ny - 2) * nx + x;
@@ -186,6 +184,7 @@ __device__ __forceinline__ void wall_gather(const WallArgs& a, int x, int y, flo
     }
   });
   const double sm1 = (B - A) / (W + A);            // s - 1
+  float* comp = a.comp + (size_t)(3 * side + r) * 37 * nx + x;
   static_for<37>([&](auto I) {
     constexpr int i = I;
     constexpr int cy = L::c(i, 1), ab = cy < 0 ? -cy : cy;
@@ -194,9 +193,25 @@ __device__ __forceinline__ void wall_gather(const WallArgs& a, int x, int y, flo
       if (y - cy < 0 || y - cy >= ny) {
         const double pi = peq_m1_hp<i>(hpt[ab - 1]), pb = peq_m1_hp<b>(hpp);
         // s P_i - P_ibar = (s - 1) + s (P_i - 1) - (P_ibar - 1)
-        g[i] = (float)fma(rp, sm1 + fma(sm1, pi, pi) - pb, (double)ldpop<ST>(a, b, x, y));
+        comp[(size_t)i * nx] = (float)fma(rp, sm1 + fma(sm1, pi, pi) - pb, (double)ldpop<ST>(a, b, x, y));
       }
     }
+  });
+}
+
+// The 37 populations of node (x, y) at time t after streaming, the unknowns
+// at the walls taken from the completion launch.
+template <int ST>
+__device__ __forceinline__ void wall_gather(const WallArgs& a, int x, int y, float (&g)[37]) {
+  const int nx = a.nx, ny = a.ny;
+  const int side = (y < ny / 2) ? 0 : 1;
+  const int r = side == 0 ? y : ny - 1 - y;
+  const float* comp = a.comp + (size_t)(3 * side + (r < 3 ? r : 0)) * 37 * nx + x;
+  static_for<37>([&](auto I) {
+    constexpr int i = I;
+    constexpr int cx = L::c(i, 0), cy = L::c(i, 1);
+    const int ys = y - cy;
+    g[i] = (ys >= 0 && ys < ny) ? ldpop<ST>(a, i, wrapx(x - cx, nx), ys) : __ldg(comp + (size_t)i * nx);
   });
 }
 
@@ -437,8 +452,24 @@ __global__ void __launch_bounds__(256) wall_init_kernel(const __grid_constant__ 
   });
 }
 
+// One thread per node of the six wall rows (rows 0, 1, 2 and ny - 1, ny - 2,
+// ny - 3), one warp per block so that the FP64 work spreads over the SMs.
 template <int ST>
-cudaError_t launch_walls_st(const WallArgs& a, bool collide, bool thermal, cudaStream_t s) {
+__global__ void __launch_bounds__(32) wall_complete_kernel(const __grid_constant__ WallArgs a) {
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  if (t >= 6 * a.nx) return;
+  const int slot = t / a.nx, x = t - slot * a.nx;
+  const int y = slot < 3 ? slot : a.ny - 1 - (slot - 3);
+  wall_complete<ST>(a, x, y);
+}
+
+template <int ST>
+cudaError_t launch_walls_st(const WallArgs& a, int mode, bool thermal, cudaStream_t s) {
+  if (mode == 2) {
+    wall_complete_kernel<ST><<<(6 * a.nx + 31) / 32, 32, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  const bool collide = mode == 1;
   const dim3 block(kBX, kBY), grid((a.nx + kBX - 1) / kBX, (a.ny + kBY - 1) / kBY);
   if (!collide)
     wall_moments_kernel<ST><<<grid, block, 0, s>>>(a);
@@ -462,11 +493,11 @@ cudaError_t launch_wall_init(const WallArgs& a, int storage, const float* rho, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_walls(const WallArgs& a, int storage, bool collide, bool thermal, cudaStream_t s) {
+cudaError_t launch_walls(const WallArgs& a, int storage, int mode, bool thermal, cudaStream_t s) {
   switch (storage) {
-    case ST_F32: return launch_walls_st<ST_F32>(a, collide, thermal, s);
-    case ST_F16: return launch_walls_st<ST_F16>(a, collide, thermal, s);
-    default: return launch_walls_st<ST_BF16>(a, collide, thermal, s);
+    case ST_F32: return launch_walls_st<ST_F32>(a, mode, thermal, s);
+    case ST_F16: return launch_walls_st<ST_F16>(a, mode, thermal, s);
+    default: return launch_walls_st<ST_BF16>(a, mode, thermal, s);
   }
 }
 
