@@ -84,8 +84,10 @@ typedef enum {
  * population turned back (r - |c_iy| / 2 rows from the wall node), and s
  * keeps the mass that left equal to the mass returned (impermeable wall).
  * grad theta for H_i is one-sided into the fluid at the wall rows.  Each step
- * is two launches (moments, then collision); the context keeps the previous
- * step's moments (4 N floats, part of the state that hlbm_save writes). */
+ * is three launches (the completion of the six wall rows, in FP64; moments;
+ * collision); the context keeps the previous step's moments (4 N floats, part
+ * of the state that hlbm_save writes) and a 6 x 37 x nx float buffer of
+ * completed populations (workspace, rebuilt every step). */
 #define HLBM_WALLS 32u
 /* In-place step (D2Q37, periodic): one population buffer instead of two (the
  * AA pattern: even steps collide in place and store each result in the
