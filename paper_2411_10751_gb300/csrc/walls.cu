@@ -309,7 +309,7 @@ __device__ __forceinline__ WallMoments wall_moments(const WallArgs& a, float (&g
 }
 
 template <int ST>
-__global__ void __launch_bounds__(kBX * kBY) wall_moments_kernel(const __grid_constant__ WallArgs a) {
+__global__ void __launch_bounds__(kBX * kBY, 4) wall_moments_kernel(const __grid_constant__ WallArgs a) {
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   const bool active = x < a.nx && y < a.ny;
   double v[6] = {0, 0, 0, 0, 0, 0};
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kBX * kBY) wall_moments_kernel(const __grid_co
 }
 
 template <int ST, bool THERMAL>
-__global__ void __launch_bounds__(kBX * kBY) wall_collide_kernel(const __grid_constant__ WallArgs a) {
+__global__ void __launch_bounds__(kBX * kBY, 3) wall_collide_kernel(const __grid_constant__ WallArgs a) {
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const int nx = a.nx, ny = a.ny;
