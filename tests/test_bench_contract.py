@@ -48,3 +48,23 @@ def test_launch_count_and_multistep_rule():
     drop = W.droplet(n=512)
     assert not bench._multistep(drop, (4, 1, 3))              # frame 3 + pull 3 exceeds a 4-row tile
     assert bench._multistep(drop, (8, 1, 3))
+
+
+def test_every_workload_builds_with_its_byte_count():
+    """Each bench workload constructs with finite fields of its stated size;
+    the algorithmic bytes per node follow the storage, the lattice and the
+    in-place step's neighbour field; the wall step counts its three launches."""
+    import numpy as np
+    for name, (make, desc) in bench.WORKLOADS.items():
+        if name in ("kolmogorov4096", "thermal4096", "tg3d256", "kolmogorov4096_aa"):
+            continue   # the same constructors at a size too large for a quick CPU check
+        c = make()
+        assert desc and c.rho.shape == ((c.ny, c.nx) if c.lattice == "D2Q37" else (c.nz, c.ny, c.nx)), name
+        for f in (c.rho, c.u, c.theta):
+            assert np.isfinite(f).all(), name
+        q = 37 if c.lattice == "D2Q37" else 39
+        lag = 8 if c.params.get("lag") and (c.params.get("H") or c.params.get("SC")) else 0
+        assert bench._bytes_per_node(c, "f32") == 2 * q * 4 + lag, name
+        assert bench._bytes_per_node(c, "f16") == 2 * q * 2 + lag, name
+    rb = bench.WORKLOADS["rb1024"][0]()
+    assert rb.params.get("walls") and bench._launches(rb, (8, 1, 1), 20) == 60
